@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the matrix-profile self-join on one GB300 (or N replicas).
+
+Workload: self-join of a 2^20-sample float32 random walk with three planted
+motif pairs and a planted discord, window m = 256, exclusion zone
+ceil(m/2) = 128, in the FP32-mixed precision (FP64 statistics, anchors and
+distances; FP32 diagonal recurrence).  One step = one whole mp_selfjoin
+(input conversion, statistics, tile planning, the persistent diagonal-tile
+kernel, finalize with the exact FP64 refine) on input already resident in
+HBM.  The all-FP64 kernel is timed on the same input for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+replica of the workload (no collective on the data path); the timed region
+is bracketed by a barrier and a synchronize, and the slowest rank's time is
+reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "self-join Gcells/s @n=2^20,m=256: FP32-mixed vs FP64 GPU; % FP32 peak"
+N_DEFAULT, M_DEFAULT, SEED = 1 << 20, 256, 2024
+PROFILE_JSON = os.path.join(ROOT, "profiles", "join_f32_selfjoin_n2p20_m256.json")
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def selfjoin_cells(l: int, E: int) -> int:
+    """Admissible unordered pairs of a self-join: diagonals E..l-1."""
+    k = l - E
+    return k * (k + 1) // 2 if k > 0 else 0
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1904_12626_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(n: int, m: int):
+    from paper_1904_12626_gb300 import synth
+    x, info = synth.planted_walk(n, m, seed=SEED)
+    return x, info
+
+
+def cpu_oracle_rate(x, m: int, E: int, target_s: float, rows_min: int = 8):
+    """Time the CPU oracle on a seeded sample of rows; returns
+    (cells_per_s of the whole job extrapolated, rows, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    from paper_1904_12626_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    x64 = np.asarray(x, dtype=np.float64)
+    l = len(x64) - m + 1
+    cells = selfjoin_cells(l, E)
+    rows = max(rows_min, cores)
+    t0 = time.perf_counter()
+    oracle.selfjoin(x64, m, rows=synth.sample_rows(l, rows, seed=99))
+    dt = time.perf_counter() - t0
+    if dt < target_s:
+        more = int(rows * (target_s - dt) / max(dt, 1e-3))
+        more = max(0, min(more, 64 * cores))
+        if more:
+            t1 = time.perf_counter()
+            oracle.selfjoin(x64, m, rows=synth.sample_rows(l, more, seed=100))
+            dt2 = time.perf_counter() - t1
+            rows, dt = rows + more, dt + dt2
+    per_row = dt / rows
+    return cells / (per_row * l), rows, dt, cores
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_1904_12626_gb300 import synth  # noqa: F401 - input recipe only
+    x, _ = workload(args.n, args.m)
+    E = math.ceil(0.5 * args.m)
+    l = args.n - args.m + 1
+    cells = selfjoin_cells(l, E)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(x, args.m, E, target_s=args.ref_step_s / 4)
+    rates, rows_total, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        r, rows, dt, cores = cpu_oracle_rate(x, args.m, E, target_s=args.ref_step_s)
+        rates.append(r)
+        rows_total += rows
+        secs += dt
+    value = statistics.median(rates) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gcells/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": cells / (value * 1e9) * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(args, E, cells),
+        "cpu_baseline": {"value": value, "unit": "Gcells/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows_total} seeded rows of the n={args.n} self-join in "
+                                   f"{secs:.1f} s, extrapolated to all {l} rows"},
+        "e2e": {"value": value, "unit": "Gcells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(args, E, cells):
+    return {"workload": f"self-join, planted random walk n={args.n} float32, m={args.m}, ez=0.5 "
+                        f"(E={E}), FP32-mixed", "n": args.n, "m": args.m, "cells": cells,
+            "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def traffic_from_profile():
+    if not os.path.exists(PROFILE_JSON):
+        return None
+    with open(PROFILE_JSON) as fh:
+        p = json.load(fh)
+    if p.get("csrc_sha") != csrc_digest():
+        return None
+    return p.get("dram_bytes_per_launch")
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, build
+    build.build()
+    api.init()
+    lib = _lib.load()
+    x_np, info = workload(args.n, args.m)
+    n, m = args.n, args.m
+    E = math.ceil(0.5 * m)
+    l = n - m + 1
+    cells = selfjoin_cells(l, E)
+    x = torch.from_numpy(x_np).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    import ctypes
+    cfg = _lib.make_config(m, 0.5, args.prec)
+    ws = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg)), x.device)
+    _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
+
+    def step(prec):
+        return api.selfjoin(x, m, 0.5, prec, ws=ws)
+
+    for _ in range(args.warmup):
+        step(args.prec)
+    torch.cuda.synchronize()
+    api.device_status(ws)
+
+    launches_per_step = 6          # convert, descriptors, stats, plan, tile kernel, finalize
+    step_ms, kern_ms = [], []
+    kms = ctypes.c_float()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            step(args.prec)
+            e.record()
+            e.synchronize()
+            step_ms.append(s.elapsed_time(e))
+            _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+            kern_ms.append(kms.value)
+    torch.cuda.synchronize()
+    barrier(world)
+    api.device_status(ws)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    kernel_ms = max_over_ranks(statistics.mean(kern_ms), world)
+    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
+
+    # all-FP64 kernel on the same input (comparison leg, one warm-up + timed steps)
+    fp64 = None
+    if not args.skip_fp64:
+        cfg64 = _lib.make_config(m, 0.5, "fp64")
+        ws64 = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg64)), x.device)
+        api.selfjoin(x, m, 0.5, "fp64", ws=ws64)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            api.selfjoin(x, m, 0.5, "fp64", ws=ws64)
+            e.record()
+            e.synchronize()
+            t64.append(s.elapsed_time(e))
+        _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+        ms64 = max_over_ranks(statistics.mean(t64), world)
+        fp64 = {"value": cells / (ms64 / 1e3) / 1e9, "unit": "Gcells/s", "ms_per_step": ms64,
+                "kernel_ms": kms.value}
+        del ws64
+
+    # end to end through the public API: pinned host input in, MP/PI back to host
+    xh = torch.from_numpy(x_np).pin_memory()
+    mph = torch.empty(l, dtype=torch.float64).pin_memory()
+    pih = torch.empty(l, dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        xd = xh.to("cuda", non_blocking=True)
+        a, b = api.selfjoin(xd, m, 0.5, args.prec, ws=ws)
+        mph.copy_(a, non_blocking=True)
+        pih.copy_(b, non_blocking=True)
+        e.record()
+        e.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(s.elapsed_time(e))
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+    e2e_value = world * cells * args.steps / (e2e_total / 1e3) / 1e9
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(0)
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    clocks = clk.summary()
+    sms = props.multi_processor_count
+    issue_peak = sms * 128 * f_max * 1e6 / 1e12            # T FP32 lane-instructions / s
+    cells_per_s_kernel = cells / (kernel_ms / 1e3)
+    achieved = 6 * cells_per_s_kernel / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)",
+        "data": "synthetic", "config": config_block(args, E, cells),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
+                     "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
+                     "frac": achieved / issue_peak, "traffic": traffic_from_profile(),
+                     "kernel": "join_tile_kernel<TraitsF32,8,4,256>", "kernel_ms": kernel_ms,
+                     "peak_basis": f"{sms} SMs x 128 lanes x {f_max:.0f} MHz "
+                                   f"({'measured max clock' if peaks else 'nominal max clock'})",
+                     "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),
+                     "frac_at_median_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                              if clocks.get("sm_mhz") else None)},
+        "fp64": fp64,
+        "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None,
+        "e2e": {"value": e2e_value, "unit": "Gcells/s", "h2d_bytes_per_step": 4 * n,
+                "d2h_bytes_per_step": 16 * l},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if not args.skip_cpu:
+        rate, rows, secs, cores = cpu_oracle_rate(x_np, m, E, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gcells/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{rows} seeded rows of the n={n} self-join in {secs:.1f} s, "
+                                          f"extrapolated to all {l} rows"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--m", type=int, default=M_DEFAULT)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-s", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if world > 1:
+        args.gpus = world
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

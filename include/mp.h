@@ -1,0 +1,220 @@
+/*
+ * mp.h -- C ABI of libmpgb, a matrix profile library for one NVIDIA GB300.
+ *
+ * The matrix profile (MP) of a series is, for every length-m subsequence, the
+ * Euclidean distance between z-normalised subsequences to its nearest
+ * neighbour in the join set; the profile index (PI) is that neighbour's
+ * position (tsmp paper, Sec. 2 "The matrix profile").  A self-join takes one
+ * series and skips trivial matches inside an exclusion zone; an AB-join takes
+ * two series (Sec. 3.2 "Input arguments and example").  The library computes
+ * both exactly, in the diagonal order the paper credits to SCRIMP
+ * (Sec. 3.3.3) with the dot-product reuse it credits to STOMP (Sec. 3.3.2).
+ *
+ * Conventions shared by every entry point:
+ *   - window i is x[i .. i+m-1] (0-based); l = n - m + 1 windows
+ *     (Sec. 3.4.1 and 3.4.3 print l for two inputs);
+ *   - z-normalisation uses the population standard deviation;
+ *   - exclusion zone E = ceil(ez * m) (Sec. 3.2); j is excluded from row i
+ *     iff |i - j| < E (MP_FLAG_EXCL_INCLUSIVE: iff |i - j| <= E);
+ *   - a window whose m values are all equal is "flat": every pair involving
+ *     it has correlation 0, i.e. distance sqrt(2m);
+ *   - ties go to the lowest index; a row without an admissible neighbour
+ *     gets MP = +inf and PI = -1;
+ *   - MP is FP64, PI is int64.
+ *
+ * Memory and streams: every array argument is a DEVICE pointer owned by the
+ * caller unless its comment says host.  `stream` is a cudaStream_t passed as
+ * void* (NULL = legacy default stream).  Every compute call only enqueues
+ * work on `stream`: it never synchronises, never allocates device memory and
+ * never throws.  Host-side argument checks return an error before anything
+ * is enqueued.  Errors found on the device (non-finite input, a retry limit
+ * reached) are recorded in a status word inside the caller's workspace and
+ * read back by mp_get_device_status().  All entry points are capture-safe
+ * (they may be recorded into a CUDA graph) once mp_init() has run.
+ *
+ * Workspace: each join needs scratch device memory of at least the size its
+ * *_workspace_bytes() query returns; the buffer must be 256-byte aligned and
+ * must not be used by two calls in flight at the same time.
+ */
+#ifndef MPGB_MP_H
+#define MPGB_MP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MP_OK = 0,
+    MP_EINVAL = 1,         /* bad argument (null pointer, m < 4, m > n, ...) */
+    MP_EINVAL_DATA = 2,    /* the input holds NaN or Inf (device-detected) */
+    MP_ENOMEM = 3,         /* workspace smaller than the size query says */
+    MP_ECUDA = 4,          /* a CUDA runtime call failed */
+    MP_ETIMEOUT = 5,       /* a bounded device retry loop gave up */
+    MP_EUNSUPPORTED = 6    /* no GPU of the compiled architecture, or an
+                              unsupported tile configuration */
+} mp_status;
+
+typedef enum { MP_F32 = 0, MP_F64 = 1 } mp_dtype;                  /* input element type */
+typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
+
+/* mp_config.flags */
+#define MP_FLAG_EXCL_INCLUSIVE 0x1u   /* exclude |i-j| <= E instead of < E */
+#define MP_FLAG_NO_REFINE      0x2u   /* MP from the kernel's correlation instead of
+                                         the exact FP64 distance of (i, PI[i]) */
+#define MP_FLAG_PAN_NORMALIZE  0x4u   /* mp_pan: divide each row by sqrt(2m) */
+
+/*
+ * Join parameters.  m: window length (>= 4).  ez: exclusion-zone fraction
+ * (>= 0; the paper's default is 1/2, Sec. 3.2).  prec: arithmetic of the
+ * diagonal recurrence (MP_PREC_FP32_MIXED keeps stats, anchors and the
+ * final distances in FP64).  anchor_every (K): rows between exact FP64
+ * re-anchors of each diagonal's covariance; 0 = once per tile.  tile_rows
+ * (TR): rows per tile; 0 = library default.  variant: compiled tile shape
+ * (0 = default; see mp_variant_count/mp_variant_info).  flags: MP_FLAG_*.
+ */
+typedef struct {
+    int32_t m;
+    double ez;
+    int32_t prec;
+    int32_t anchor_every;
+    int32_t tile_rows;
+    int32_t variant;
+    uint32_t flags;
+} mp_config;
+
+/* Fill `cfg` with the defaults for window m (ez 1/2, FP32-mixed, refine on). */
+void mp_config_default(mp_config *cfg, int32_t m);
+
+/* Host helpers, no GPU needed.  l = n - m + 1 (0 if m > n or m < 1), per the
+ * sizes printed in Sec. 3.4.1/3.4.3; E = ceil(ez * m), per Sec. 3.2 (the
+ * worked value 50 * 1/4 -> 13 in Sec. 3.4.3 fixes the rounding). */
+int64_t mp_profile_length(int64_t n, int32_t m);
+int64_t mp_exclusion_zone(int32_t m, double ez);
+
+/* Library version string and the tile-shape variants compiled in.  Host only. */
+const char *mp_version(void);
+int32_t mp_variant_count(int32_t prec);
+/* For variant v of precision prec: diagonals per tile (TD) and rows per
+ * shared-memory chunk (RC).  Returns MP_EINVAL for an unknown variant. */
+mp_status mp_variant_info(int32_t prec, int32_t v, int32_t *tile_diags, int32_t *chunk_rows);
+
+/* Human-readable name of a status code (static storage). */
+const char *mp_status_string(mp_status st);
+
+/*
+ * Check that a GPU of the compiled architecture (sm_103) is present, select
+ * it as current if `device` >= 0, and cache per-device launch limits.  Calls
+ * on a device run this themselves on first use; call it once before
+ * recording any entry point into a CUDA graph.
+ */
+mp_status mp_init(int32_t device);
+
+/*
+ * Per-window statistics (the quantities the z-normalised distance and the
+ * diagonal recurrence are built from; the paper's brute-force definition is
+ * Sec. 2, the reuse of dot products Sec. 3.3.2):
+ *   mu[i]   mean of window i;
+ *   invn[i] 1 / ||x_i - mu_i||_2 (0 for a flat window);
+ *   df[i]   (x[i+m-1] - x[i-1]) / 2, df[0] = 0;
+ *   dg[i]   (x[i+m-1] - mu_i) + (x[i-1] - mu_{i-1}), dg[0] = 0;
+ *   flat[i] 1 iff the m values of window i are all equal.
+ * With c(i,j) the centred dot product of windows i and j,
+ * c(i,j) = c(i-1,j-1) + df[i]*dg[j] + df[j]*dg[i].
+ * x: n elements of `dtype`.  All outputs have l entries; any output pointer
+ * may be NULL to skip it.  Sums are compensated (double-double).
+ */
+mp_status mp_stats(const void *x, int32_t dtype, int64_t n, int32_t m,
+                   double *mu, double *invn, double *df, double *dg, uint8_t *flat,
+                   void *stream);
+
+/*
+ * Self-join (Sec. 3.2, one series).  x: n elements of `dtype`.
+ * mp: l doubles, pi: l int64 (outputs, overwritten).  ws/ws_bytes: scratch
+ * of at least mp_selfjoin_workspace_bytes(n, cfg) bytes.
+ */
+size_t mp_selfjoin_workspace_bytes(int64_t n, const mp_config *cfg);
+mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                      double *mp, int64_t *pi, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * AB-join (Sec. 3.2, two series; no exclusion zone).  For every window of a:
+ * the nearest window of b (mp_a, pi_a: la entries).  For every window of b:
+ * the nearest window of a (mp_b, pi_b: lb entries; both may be NULL to skip
+ * that side).  a and b share `dtype`.
+ */
+size_t mp_abjoin_workspace_bytes(int64_t na, int64_t nb, const mp_config *cfg);
+mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_t dtype,
+                    const mp_config *cfg, double *mp_a, int64_t *pi_a,
+                    double *mp_b, int64_t *pi_b, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Batched ragged self-joins in one persistent launch: series b is
+ * values[offsets[b] .. offsets[b+1]) with window ms[b] (cfg->m is ignored;
+ * cfg->ez, prec and flags apply to all).  offsets: B+1 int64 (device),
+ * ms: B int32 (device), out_offsets: B+1 int64 (device) with
+ * out_offsets[b+1] - out_offsets[b] >= l_b; series b's MP/PI go to
+ * mp/pi[out_offsets[b] ..).  A series with l_b <= 0 writes nothing.
+ * total_values = offsets[B] and max_m bound the workspace (host values).
+ */
+size_t mp_batched_workspace_bytes(int64_t total_values, int32_t B, int32_t max_m,
+                                  const mp_config *cfg);
+mp_status mp_batched(const void *values, int32_t dtype, int64_t total_values,
+                     const int64_t *offsets, const int32_t *ms, int32_t B, int32_t max_m,
+                     const mp_config *cfg, double *mp, int64_t *pi, const int64_t *out_offsets,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Pan matrix profile: the self-join of one series at every window size in
+ * ms (host array of nm sizes, each >= 4 and <= n), in one persistent launch.
+ * pan and pi are row-major [nm x (n - min(ms) + 1)]; row k holds the MP/PI
+ * for window ms[k] in its first n - ms[k] + 1 entries and +inf / -1 after.
+ * MP_FLAG_PAN_NORMALIZE divides each MP row by sqrt(2 ms[k]).
+ */
+size_t mp_pan_workspace_bytes(int64_t n, const int32_t *ms, int32_t nm, const mp_config *cfg);
+mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int32_t nm,
+                 const mp_config *cfg, double *pan, int64_t *pi, void *ws, size_t ws_bytes,
+                 void *stream);
+
+/*
+ * Gradient of L = sum_i grad_mp[i] * MP[i] with respect to x, holding each
+ * argmin pair (i, pi[i]) fixed.  With z_i, z_j the z-normalised windows,
+ * rho their correlation, d their distance and sigma the population standard
+ * deviations:
+ *   dMP_i/dx[i+k] = -(z_j[k] - rho z_i[k]) / (sigma_i d)
+ *   dMP_i/dx[j+k] = -(z_i[k] - rho z_j[k]) / (sigma_j d)
+ * A row contributes nothing when pi[i] < 0, either window is flat, or
+ * d < 1e-12.  (The paper has no gradient; this is the derivative of the
+ * Sec. 2 distance.)  x: n of dtype; pi: l int64; grad_mp: l doubles;
+ * grad_x: n doubles, overwritten.
+ */
+size_t mp_backward_workspace_bytes(int64_t n, int32_t m);
+mp_status mp_backward(const void *x, int32_t dtype, int64_t n, int32_t m, const int64_t *pi,
+                      const double *grad_mp, double *grad_x, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/*
+ * Diagnostics.  While enabled (process-wide, off by default), every join
+ * records a pair of CUDA events on the caller's stream around its tile
+ * kernel (the persistent diagonal-tile launch), on the current device;
+ * mp_timing_last_ms() waits for the most recent pair and returns the
+ * kernel's elapsed milliseconds.  Leave it disabled while recording a join
+ * into a CUDA graph.
+ */
+mp_status mp_timing_enable(int32_t on);
+mp_status mp_timing_last_ms(float *ms);
+
+/*
+ * Synchronise `stream`, read the status word of workspace `ws` (the one the
+ * preceding calls used), clear it, and return it (MP_OK if no device-side
+ * error was recorded).
+ */
+mp_status mp_get_device_status(void *ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPGB_MP_H */

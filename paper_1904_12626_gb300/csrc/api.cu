@@ -1,0 +1,544 @@
+// api.cu -- the C ABI (include/mp.h): argument checks, workspace layout and the
+// launch sequence of every join.  Host code only; the kernels live in the
+// other translation units.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+using namespace mpgb;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kDefaultTileRowsF32 = 8192;
+constexpr int kDefaultTileRowsF64 = 4096;
+constexpr long long kMaxN = 2147483647ll;
+
+struct DeviceInfo {
+    bool ready = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};     // timing diagnostics
+    bool ev_used = false;
+    bool ok = false;
+    int sms = 0;
+    int f32_bps[8] = {0};
+    int f64_bps[8] = {0};
+};
+DeviceInfo g_dev[kMaxDevices];
+std::mutex g_mu;
+bool g_timing = false;
+int g_timing_dev = -1;
+
+mp_status device_info(int dev, const DeviceInfo **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return MP_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo &d = g_dev[dev];
+    if (!d.ready) {
+        cudaDeviceProp p;
+        if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return MP_ECUDA;
+        d.ok = (p.major == 10 && p.minor == 3);
+        d.sms = p.multiProcessorCount;
+        if (d.ok) {
+            int cur = -1;
+            cudaGetDevice(&cur);
+            if (cur != dev) cudaSetDevice(dev);
+            for (int v = 0; v < f32_variant_count() && v < 8; ++v) d.f32_bps[v] = f32_blocks_per_sm(v);
+            for (int v = 0; v < f64_variant_count() && v < 8; ++v) d.f64_bps[v] = f64_blocks_per_sm(v);
+            if (cur != dev && cur >= 0) cudaSetDevice(cur);
+        }
+        d.ready = true;
+    }
+    *out = &d;
+    return d.ok ? MP_OK : MP_EUNSUPPORTED;
+}
+
+mp_status current_device(const DeviceInfo **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MP_ECUDA;
+    return device_info(dev, out);
+}
+
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// resolved tile configuration of a call
+struct TileCfg {
+    int fp64;
+    int variant;
+    int tile_diags;
+    int chunk_rows;
+    int tile_rows;
+    int anchor_every;
+    bool refine;
+};
+
+mp_status resolve(const mp_config *cfg, TileCfg *t)
+{
+    if (!cfg) return MP_EINVAL;
+    if (cfg->prec != MP_PREC_FP64 && cfg->prec != MP_PREC_FP32_MIXED) return MP_EINVAL;
+    if (!(cfg->ez >= 0.0) || !std::isfinite(cfg->ez)) return MP_EINVAL;
+    if (cfg->anchor_every < 0 || cfg->tile_rows < 0) return MP_EINVAL;
+    t->fp64 = cfg->prec == MP_PREC_FP64;
+    t->variant = cfg->variant;
+    int threads = 0, smem = 0;
+    const bool ok = t->fp64 ? f64_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem)
+                            : f32_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem);
+    if (!ok) return MP_EUNSUPPORTED;
+    const int rc = t->chunk_rows;
+    int tr = cfg->tile_rows > 0 ? cfg->tile_rows : (t->fp64 ? kDefaultTileRowsF64 : kDefaultTileRowsF32);
+    tr = (int)(ceil_div(tr, rc) * rc);
+    t->tile_rows = tr;
+    t->anchor_every = cfg->anchor_every > 0 ? (int)(ceil_div(cfg->anchor_every, rc) * rc) : 0;
+    if (t->anchor_every >= tr) t->anchor_every = 0;
+    t->refine = (cfg->flags & MP_FLAG_NO_REFINE) == 0;
+    return MP_OK;
+}
+
+// Workspace layout shared by every join.
+struct LayoutReq {
+    long long nx = 0;        // FP64 copy of the input values
+    long long S = 0;         // stats-index space
+    int nsets = 0, nprob = 0, nfin = 0;
+    long long max_bands = 0;
+    int fp64 = 0;
+};
+
+struct Layout {
+    Hdr *hdr;
+    double *x64, *mu;
+    float4 *s32;
+    D4 *s64;
+    char *keys;
+    StatSet *sets;
+    Prob *probs;
+    FinDesc *fins;
+    long long *band_off;
+    Band *bands;
+    unsigned long long *tile_prefix;
+    size_t bytes;
+};
+
+Layout carve(void *base, const LayoutReq &r)
+{
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        const size_t o = (off + 255) & ~(size_t)255;
+        off = o + bytes;
+        return base ? (void *)((char *)base + o) : nullptr;
+    };
+    const size_t ksz = r.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    L.hdr = (Hdr *)take(256);
+    L.x64 = (double *)take(sizeof(double) * (size_t)r.nx);
+    L.mu = (double *)take(sizeof(double) * (size_t)r.S);
+    L.s32 = r.fp64 ? nullptr : (float4 *)take(sizeof(float4) * (size_t)r.S);
+    L.s64 = (D4 *)take(sizeof(D4) * (size_t)r.S);
+    L.keys = (char *)take(ksz * (size_t)r.S);
+    L.sets = (StatSet *)take(sizeof(StatSet) * (size_t)r.nsets);
+    L.probs = (Prob *)take(sizeof(Prob) * (size_t)r.nprob);
+    L.fins = (FinDesc *)take(sizeof(FinDesc) * (size_t)r.nfin);
+    L.band_off = (long long *)take(sizeof(long long) * (size_t)(r.nprob + 1));
+    L.bands = (Band *)take(sizeof(Band) * (size_t)(r.max_bands > 0 ? r.max_bands : 1));
+    L.tile_prefix = (unsigned long long *)take(sizeof(unsigned long long) * (size_t)(r.max_bands + 1));
+    L.bytes = (off + 255) & ~(size_t)255;
+    return L;
+}
+
+bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
+
+#define MP_CU(call)                                   \
+    do {                                              \
+        if ((call) != cudaSuccess) return MP_ECUDA;   \
+    } while (0)
+
+// stats -> keys reset -> plan -> persistent join -> finalize
+mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
+                   const DeviceInfo *dev, cudaStream_t st)
+{
+    MP_CU(launch_stats_sets(L.sets, r.nsets, r.S, L.mu, L.s32, L.s64, st));
+    const size_t ksz = r.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    MP_CU(cudaMemsetAsync(L.keys, 0, ksz * (size_t)r.S, st));
+    MP_CU(launch_plan(L.probs, r.nprob, t.tile_diags, t.tile_rows, L.band_off, L.bands,
+                      L.tile_prefix, r.max_bands, L.hdr, st));
+    const int bps = t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant];
+    if (bps <= 0) return MP_EUNSUPPORTED;
+    const int grid = dev->sms * bps;
+    DeviceInfo *dm = const_cast<DeviceInfo *>(dev);
+    const bool timing = g_timing && dm->ev[0] != nullptr;
+    if (timing) MP_CU(cudaEventRecord(dm->ev[0], st));
+    if (t.fp64)
+        MP_CU(launch_join_f64(t.variant, L.probs, L.bands, L.tile_prefix, L.hdr, t.tile_rows,
+                              t.anchor_every, grid, st));
+    else
+        MP_CU(launch_join_f32(t.variant, L.probs, L.bands, L.tile_prefix, L.hdr, t.tile_rows,
+                              t.anchor_every, grid, st));
+    if (timing) {
+        MP_CU(cudaEventRecord(dm->ev[1], st));
+        dm->ev_used = true;
+    }
+    MP_CU(launch_finalize(L.fins, r.nfin, max_fin_len, t.fp64, t.refine ? 1 : 0, st));
+    return MP_OK;
+}
+
+bool valid_dtype(int32_t dtype) { return dtype == MP_F32 || dtype == MP_F64; }
+
+LayoutReq self_req(int64_t n, int32_t m, const TileCfg &t)
+{
+    LayoutReq r;
+    const long long l = n - m + 1;
+    r.nx = n;
+    r.S = n + kPad;
+    r.nsets = r.nprob = r.nfin = 1;
+    r.max_bands = ceil_div(l > 0 ? l : 0, t.tile_diags) + 1;
+    r.fp64 = t.fp64;
+    return r;
+}
+
+LayoutReq ab_req(int64_t na, int64_t nb, int32_t m, const TileCfg &t)
+{
+    LayoutReq r;
+    r.nx = na + nb;
+    r.S = na + nb + 2 * (long long)kPad;
+    r.nsets = r.nprob = r.nfin = 2;
+    r.max_bands = ceil_div(na, t.tile_diags) + ceil_div(nb, t.tile_diags) + 2;
+    r.fp64 = t.fp64;
+    (void)m;
+    return r;
+}
+
+LayoutReq pan_req(int64_t n, const int32_t *ms, int32_t nm, const TileCfg &t)
+{
+    LayoutReq r;
+    r.nx = n;
+    r.S = (long long)nm * (n + kPad);
+    r.nsets = r.nprob = r.nfin = nm;
+    long long b = 0;
+    for (int k = 0; k < nm; ++k) b += ceil_div(n - ms[k] + 1, t.tile_diags) + 1;
+    r.max_bands = b;
+    r.fp64 = t.fp64;
+    return r;
+}
+
+LayoutReq batched_req(int64_t total, int32_t B, const TileCfg &t)
+{
+    LayoutReq r;
+    r.nx = total;
+    r.S = total + (long long)B * kPad;
+    r.nsets = r.nprob = r.nfin = B;
+    r.max_bands = ceil_div(total, t.tile_diags) + B;
+    r.fp64 = t.fp64;
+    return r;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mp_config_default(mp_config *cfg, int32_t m)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->m = m;
+    cfg->ez = 0.5;
+    cfg->prec = MP_PREC_FP32_MIXED;
+    cfg->anchor_every = 0;
+    cfg->tile_rows = 0;
+    cfg->variant = 0;
+    cfg->flags = 0;
+}
+
+int64_t mp_profile_length(int64_t n, int32_t m)
+{
+    if (m < 1 || (int64_t)m > n) return 0;
+    return n - (int64_t)m + 1;
+}
+
+int64_t mp_exclusion_zone(int32_t m, double ez) { return (int64_t)std::ceil(ez * (double)m); }
+
+const char *mp_version(void) { return "mpgb 0.1 (sm_103a)"; }
+
+int32_t mp_variant_count(int32_t prec)
+{
+    return prec == MP_PREC_FP64 ? f64_variant_count() : f32_variant_count();
+}
+
+mp_status mp_variant_info(int32_t prec, int32_t v, int32_t *tile_diags, int32_t *chunk_rows)
+{
+    int td = 0, rc = 0, th = 0, sm = 0;
+    const bool ok = prec == MP_PREC_FP64 ? f64_variant_info(v, &td, &rc, &th, &sm)
+                                         : f32_variant_info(v, &td, &rc, &th, &sm);
+    if (!ok) return MP_EINVAL;
+    if (tile_diags) *tile_diags = td;
+    if (chunk_rows) *chunk_rows = rc;
+    return MP_OK;
+}
+
+const char *mp_status_string(mp_status st)
+{
+    switch (st) {
+    case MP_OK: return "ok";
+    case MP_EINVAL: return "invalid argument";
+    case MP_EINVAL_DATA: return "input holds NaN or Inf";
+    case MP_ENOMEM: return "workspace too small";
+    case MP_ECUDA: return "CUDA runtime error";
+    case MP_ETIMEOUT: return "device retry limit reached";
+    case MP_EUNSUPPORTED: return "unsupported device or configuration";
+    }
+    return "unknown status";
+}
+
+mp_status mp_init(int32_t device)
+{
+    if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return MP_ECUDA;
+    const DeviceInfo *d = nullptr;
+    return current_device(&d);
+}
+
+mp_status mp_stats(const void *x, int32_t dtype, int64_t n, int32_t m, double *mu, double *invn,
+                   double *df, double *dg, uint8_t *flat, void *stream)
+{
+    if (!x || !valid_dtype(dtype) || m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    const DeviceInfo *d = nullptr;
+    const mp_status s = current_device(&d);
+    if (s != MP_OK) return s;
+    MP_CU(launch_stats_public(x, dtype, n, m, mu, invn, df, dg, flat, (cudaStream_t)stream));
+    return MP_OK;
+}
+
+size_t mp_selfjoin_workspace_bytes(int64_t n, const mp_config *cfg)
+{
+    TileCfg t;
+    if (resolve(cfg, &t) != MP_OK || n < 1) return 0;
+    return carve(nullptr, self_req(n, cfg->m, t)).bytes;
+}
+
+mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *cfg, double *mp,
+                      int64_t *pi, void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!x || !mp || !pi || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const int32_t m = cfg->m;
+    if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    const LayoutReq r = self_req(n, m, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(x, dtype, n, L.x64, L.hdr, st));
+    FamilyParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.kind = 0; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez; F.flags = cfg->flags;
+    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mp_a = mp; F.pi_a = (long long *)pi; F.out_stride = 0;
+    F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
+    MP_CU(launch_family_descs(F, st));
+    return run_join(L, r, t, n - m + 1, d, st);
+}
+
+size_t mp_abjoin_workspace_bytes(int64_t na, int64_t nb, const mp_config *cfg)
+{
+    TileCfg t;
+    if (resolve(cfg, &t) != MP_OK || na < 1 || nb < 1) return 0;
+    return carve(nullptr, ab_req(na, nb, cfg->m, t)).bytes;
+}
+
+mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_t dtype,
+                    const mp_config *cfg, double *mp_a, int64_t *pi_a, double *mp_b, int64_t *pi_b,
+                    void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!a || !b || !mp_a || !pi_a || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
+    if ((mp_b == nullptr) != (pi_b == nullptr)) return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const int32_t m = cfg->m;
+    if (m < 4 || (int64_t)m > na || (int64_t)m > nb || na > kMaxN || nb > kMaxN) return MP_EINVAL;
+    const LayoutReq r = ab_req(na, nb, m, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(a, dtype, na, L.x64, L.hdr, st));
+    MP_CU(launch_convert(b, dtype, nb, L.x64 + na, L.hdr, st));
+    FamilyParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.kind = 1; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.na = na; F.nb = nb; F.ez = cfg->ez;
+    F.flags = cfg->flags;
+    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mp_a = mp_a; F.pi_a = (long long *)pi_a; F.mp_b = mp_b; F.pi_b = (long long *)pi_b;
+    F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
+    MP_CU(launch_family_descs(F, st));
+    const long long la = na - m + 1, lb = nb - m + 1;
+    return run_join(L, r, t, la > lb ? la : lb, d, st);
+}
+
+size_t mp_pan_workspace_bytes(int64_t n, const int32_t *ms, int32_t nm, const mp_config *cfg)
+{
+    TileCfg t;
+    if (resolve(cfg, &t) != MP_OK || !ms || nm < 1 || nm > kMaxPan || n < 1) return 0;
+    for (int k = 0; k < nm; ++k)
+        if (ms[k] < 4 || ms[k] > n) return 0;
+    return carve(nullptr, pan_req(n, ms, nm, t)).bytes;
+}
+
+mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int32_t nm,
+                 const mp_config *cfg, double *pan, int64_t *pi, void *ws, size_t ws_bytes,
+                 void *stream)
+{
+    TileCfg t;
+    if (!x || !ms || !pan || !pi || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
+    if (nm < 1 || nm > kMaxPan || n > kMaxN) return MP_EINVAL;
+    int32_t mmin = ms[0];
+    for (int k = 0; k < nm; ++k) {
+        if (ms[k] < 4 || (int64_t)ms[k] > n) return MP_EINVAL;
+        if (ms[k] < mmin) mmin = ms[k];
+    }
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const LayoutReq r = pan_req(n, ms, nm, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(x, dtype, n, L.x64, L.hdr, st));
+    FamilyParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.kind = 2; F.nm = nm; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez;
+    F.flags = cfg->flags;
+    for (int k = 0; k < nm; ++k) F.ms[k] = ms[k];
+    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mp_a = pan; F.pi_a = (long long *)pi; F.out_stride = n - mmin + 1;
+    F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
+    MP_CU(launch_family_descs(F, st));
+    return run_join(L, r, t, n - mmin + 1, d, st);
+}
+
+size_t mp_batched_workspace_bytes(int64_t total_values, int32_t B, int32_t max_m,
+                                  const mp_config *cfg)
+{
+    TileCfg t;
+    (void)max_m;
+    if (resolve(cfg, &t) != MP_OK || B < 1 || total_values < 0) return 0;
+    return carve(nullptr, batched_req(total_values, B, t)).bytes;
+}
+
+mp_status mp_batched(const void *values, int32_t dtype, int64_t total_values,
+                     const int64_t *offsets, const int32_t *ms, int32_t B, int32_t max_m,
+                     const mp_config *cfg, double *mp, int64_t *pi, const int64_t *out_offsets,
+                     void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!values || !offsets || !ms || !mp || !pi || !out_offsets || !ws || !valid_dtype(dtype) ||
+        !aligned256(ws))
+        return MP_EINVAL;
+    if (B < 1 || B > 65535 || total_values < 1 || total_values > kMaxN || max_m < 4) return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const LayoutReq r = batched_req(total_values, B, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(values, dtype, total_values, L.x64, L.hdr, st));
+    MP_CU(launch_batched_descs(offsets, ms, B, cfg->ez, cfg->flags, t.fp64, L.x64, L.mu, L.s32,
+                               L.s64, L.keys, mp, pi, out_offsets, L.sets, L.probs, L.fins, L.hdr,
+                               st));
+    // every series is at most total_values long: finalize covers that bound
+    return run_join(L, r, t, total_values, d, st);
+}
+
+size_t mp_backward_workspace_bytes(int64_t n, int32_t m)
+{
+    if (m < 4 || (int64_t)m > n) return 0;
+    const long long l = n - m + 1;
+    size_t off = 256;
+    auto take = [&](size_t b) { off = ((off + 255) & ~(size_t)255) + b; };
+    take(sizeof(double) * (size_t)n);
+    take(sizeof(double) * (size_t)l);
+    take(sizeof(double) * (size_t)l);
+    take((size_t)l);
+    return (off + 255) & ~(size_t)255;
+}
+
+mp_status mp_backward(const void *x, int32_t dtype, int64_t n, int32_t m, const int64_t *pi,
+                      const double *grad_mp, double *grad_x, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!x || !pi || !grad_mp || !grad_x || !ws || !valid_dtype(dtype) || !aligned256(ws))
+        return MP_EINVAL;
+    if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    if (ws_bytes < mp_backward_workspace_bytes(n, m)) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    mp_status s = current_device(&d);
+    if (s != MP_OK) return s;
+    const long long l = n - m + 1;
+    size_t off = 0;
+    auto take = [&](size_t b) -> char * {
+        const size_t o = (off + 255) & ~(size_t)255;
+        off = o + b;
+        return (char *)ws + o;
+    };
+    Hdr *hdr = (Hdr *)take(256);
+    double *x64 = (double *)take(sizeof(double) * (size_t)n);
+    double *mu = (double *)take(sizeof(double) * (size_t)l);
+    double *invn = (double *)take(sizeof(double) * (size_t)l);
+    uint8_t *flat = (uint8_t *)take((size_t)l);
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(hdr, 0, 256, st));
+    MP_CU(launch_convert(x, dtype, n, x64, hdr, st));
+    MP_CU(launch_stats_public(x64, MP_F64, n, m, mu, invn, nullptr, nullptr, flat, st));
+    MP_CU(launch_backward(x64, n, m, mu, invn, flat, pi, grad_mp, grad_x, hdr, st));
+    return MP_OK;
+}
+
+mp_status mp_timing_enable(int32_t on)
+{
+    const DeviceInfo *d = nullptr;
+    mp_status s = current_device(&d);
+    if (s != MP_OK) return s;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo &dm = g_dev[dev];
+    if (on && dm.ev[0] == nullptr) {
+        if (cudaEventCreate(&dm.ev[0]) != cudaSuccess || cudaEventCreate(&dm.ev[1]) != cudaSuccess)
+            return MP_ECUDA;
+    }
+    g_timing = on != 0;
+    g_timing_dev = dev;
+    return MP_OK;
+}
+
+mp_status mp_timing_last_ms(float *ms)
+{
+    if (!ms || g_timing_dev < 0) return MP_EINVAL;
+    DeviceInfo &dm = g_dev[g_timing_dev];
+    if (!dm.ev_used) return MP_EINVAL;
+    if (cudaEventSynchronize(dm.ev[1]) != cudaSuccess) return MP_ECUDA;
+    if (cudaEventElapsedTime(ms, dm.ev[0], dm.ev[1]) != cudaSuccess) return MP_ECUDA;
+    return MP_OK;
+}
+
+mp_status mp_get_device_status(void *ws, void *stream)
+{
+    if (!ws) return MP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MP_ECUDA;
+    unsigned v = 0;
+    if (cudaMemcpy(&v, ws, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return MP_ECUDA;
+    if (v != 0 && cudaMemset(ws, 0, sizeof(v)) != cudaSuccess) return MP_ECUDA;
+    return (mp_status)v;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// finalize.cu -- keys to (MP, PI), with the exact FP64 distance refine.
+//
+// A key holds the best correlation found for an index and the lowest
+// neighbour index reaching it.  MP = sqrt(2m(1 - rho)) (Sec. 2's z-normalised
+// Euclidean distance written through the correlation), clamped to
+// [0, 2 sqrt(m)].  With refine on (the default), MP is instead the distance
+// of the pair (i, PI[i]) recomputed directly in FP64 from the series,
+// sqrt(sum_k (z_i[k] - z_j[k])^2), which removes the error the recurrence
+// left in rho while keeping the neighbour the kernel chose.
+//
+// Flat windows (all values equal) have the closed-form answer of the
+// zero-variance convention: distance sqrt(2m) to everything, so PI is the
+// lowest admissible index.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace mpgb {
+namespace {
+
+__device__ __forceinline__ double exact_distance(const FinDesc &F, long long i, long long j,
+                                                 double invR)
+{
+    const D4 sc = F.sC[j];
+    const double s2m = sqrt(2.0 * (double)F.m);
+    if (sc.w != 0.0) return s2m;
+    const double invC = sc.z;
+    const double muR = F.muR[i], muC = F.muC[j];
+    const double *xr = F.xR + i, *xc = F.xC + j;
+    double acc = 0.0;
+    for (int t = 0; t < F.m; ++t) {
+        const double d = (xr[t] - muR) * invR - (xc[t] - muC) * invC;
+        acc = fma(d, d, acc);
+    }
+    double d = sqrt((double)F.m * acc);
+    const double cap = 2.0 * sqrt((double)F.m);
+    return d > cap ? cap : d;
+}
+
+template <bool FP64KEY>
+__device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long long l, int refine)
+{
+    const double INF = __longlong_as_double(0x7ff0000000000000ll);
+    if (i >= l) {
+        F.mp[i] = INF;
+        F.pi[i] = -1;
+        return;
+    }
+    const D4 sr = F.sR[i];
+    const double s2m = sqrt(2.0 * (double)F.m);
+    double mpv = INF;
+    long long piv = -1;
+    if (sr.w != 0.0) {
+        if (F.kmin < 0) piv = F.lC > 0 ? 0 : -1;
+        else piv = (i >= F.kmin) ? 0 : ((i + F.kmin < F.lC) ? i + F.kmin : -1);
+        if (piv >= 0) mpv = s2m;
+    } else {
+        double rho = 0.0;
+        bool have;
+        if (FP64KEY) {
+            const Key128 k = reinterpret_cast<const Key128 *>(F.key)[i];
+            have = (k.hi | k.lo) != 0ull;
+            if (have) {
+                rho = __longlong_as_double((long long)unord64(k.hi));
+                piv = (long long)(~0ull - k.lo);
+            }
+        } else {
+            const unsigned long long k = reinterpret_cast<const unsigned long long *>(F.key)[i];
+            have = k != 0ull;
+            if (have) {
+                rho = (double)__uint_as_float(unord32((unsigned)(k >> 32)));
+                piv = (long long)(0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull));
+            }
+        }
+        if (have) {
+            if (refine) {
+                mpv = exact_distance(F, i, piv, sr.z);
+            } else {
+                rho = rho > 1.0 ? 1.0 : (rho < -1.0 ? -1.0 : rho);
+                mpv = sqrt(2.0 * (double)F.m * (1.0 - rho));
+            }
+        }
+    }
+    F.mp[i] = mpv == INF ? INF : mpv * F.scale;
+    F.pi[i] = piv;
+}
+
+template <bool FP64KEY>
+__global__ void finalize_kernel(const FinDesc *__restrict__ fins, int refine)
+{
+    const FinDesc F = fins[blockIdx.y];
+    if (F.mp == nullptr || F.pi == nullptr) return;
+    const long long l = F.l > 0 ? F.l : 0;
+    const long long end = F.pad_to > l ? F.pad_to : l;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (long long)gridDim.x * blockDim.x)
+        finalize_one<FP64KEY>(F, i, l, refine);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const FinDesc *fins, int nfin, long long max_len, int fp64,
+                            int refine, cudaStream_t st)
+{
+    if (nfin <= 0 || max_len <= 0) return cudaSuccess;
+    const int threads = 256;
+    long long per = (max_len + threads - 1) / threads;       // blocks per descriptor
+    const long long cap = 65536 / nfin > 0 ? 65536 / nfin : 1;
+    if (per > cap) per = cap;
+    const dim3 grid((unsigned)per, (unsigned)nfin);
+    if (fp64)
+        finalize_kernel<true><<<grid, threads, 0, st>>>(fins, refine);
+    else
+        finalize_kernel<false><<<grid, threads, 0, st>>>(fins, refine);
+    return cudaGetLastError();
+}
+
+}  // namespace mpgb

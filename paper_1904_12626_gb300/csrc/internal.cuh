@@ -1,0 +1,205 @@
+// internal.cuh -- shared definitions of the CUDA path of libmpgb (not installed).
+//
+// Index space.  Every join works on "stats sets": one series seen through one
+// window length m.  A set with l windows owns the stats-index range
+// [sbase, sbase + l + kPad) of the workspace arrays (per-window statistics,
+// packed FP32/FP64 recurrence inputs, keys); the kPad tail entries are
+// padding the tile kernels may read past the last window (their inverse norm
+// is NaN, so every comparison against them is false).
+//
+// Problems.  A "problem" is one trapezoid of the distance matrix walked by
+// diagonals: cells (i, i+k) for row windows i of one set (R) and column
+// windows j = i+k of another (C), k in [kmin, kmax], 0 <= i < l_R,
+// 0 <= j < l_C.  A self-join is one problem (R = C, kmin = E); an AB-join is
+// two (A rows x B columns for k >= 0, B rows x A columns for k >= 1); a batch
+// or a pan profile is one problem per series or per window length.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mp.h"
+
+namespace mpgb {
+
+// padding entries after each stats set: >= the widest tile (diagonals) plus
+// one register-rotation group, see the tile kernels
+constexpr int kMaxTileDiags = 1024;
+constexpr int kMaxSlots = 16;
+constexpr int kPad = kMaxTileDiags + kMaxSlots + 16;
+
+constexpr int kWindowsPerThread = 32;     // stats kernel: windows per thread run
+constexpr unsigned kCasRetryLimit = 1u << 20;
+
+// four doubles, 32-byte aligned (two 16-byte vector loads)
+struct alignas(32) D4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, double w)
+{
+    D4 v;
+    v.x = x; v.y = y; v.z = z; v.w = w;
+    return v;
+}
+
+struct alignas(16) Key128 {               // FP64 path: (ord64(rho), ~index)
+    unsigned long long lo, hi;
+};
+
+// Workspace header (first 256 bytes of every workspace)
+struct Hdr {
+    unsigned int status;                  // first device-side mp_status != MP_OK
+    unsigned int pad0;
+    unsigned long long ticket;            // tile ticket counter of the persistent kernel
+    int nbands;                           // number of bands written by the planner
+    int pad1;
+    unsigned long long ntiles;            // number of tiles (same as tile_prefix[nbands])
+};
+
+struct StatSet {
+    const double *x;                      // FP64 series of this set
+    long long n;                          // series length
+    long long l;                          // windows (<= 0: empty set)
+    long long sbase;                      // first stats index of this set
+    int m;
+    int pad;
+};
+
+struct Prob {
+    const float4 *rS32, *cS32;            // {df, dg, invn, flat} FP32, stats-indexed
+    const D4 *rS64, *cS64;           // {df, dg, invn, flat} FP64
+    const double *rX, *cX;                // FP64 series
+    const double *rMu, *cMu;              // window means
+    void *rKey, *cKey;                    // u64 (FP32 path) or Key128 (FP64 path)
+    long long lR, lC;                     // windows of the row / column set
+    long long nC;                         // column series length
+    long long kmin, kmax;                 // inclusive diagonal range
+    int m;
+    int pad;
+};
+
+struct Band {
+    int prob;
+    int pad;
+    long long k0;                         // first diagonal of the band
+};
+
+// Finalize descriptor: one output side of one problem family
+struct FinDesc {
+    const void *key;                      // keys of this side (stats-indexed, own base)
+    const double *xR, *muR;               // own side
+    const D4 *sR;
+    const double *xC, *muC;               // candidate side
+    const D4 *sC;
+    long long l;                          // windows on this side
+    long long lC;                         // windows on the candidate side
+    long long kmin;                       // self-join: first admissible |i-j|; -1: AB
+    long long pad_to;                     // write +inf / -1 for [l, pad_to)
+    double *mp;
+    long long *pi;
+    double scale;                         // multiply MP by this (pan normalisation)
+    int m;
+    int pad;
+};
+
+// Parameters of the descriptor kernel of a self-join (kind 0), an AB-join
+// (kind 1) or a pan profile (kind 2); passed by value so that building the
+// descriptors needs no host-to-device copy (capture-safe).
+constexpr int kMaxPan = 256;
+struct FamilyParams {
+    int kind;
+    int nm;
+    int m;
+    int fp64;
+    int ms[kMaxPan];
+    const double *x64;
+    long long n, na, nb;
+    double ez;
+    unsigned flags;
+    unsigned pad;
+    double *mu;
+    float4 *s32;
+    D4 *s64;
+    char *keys;
+    double *mp_a;
+    long long *pi_a;
+    double *mp_b;
+    long long *pi_b;
+    long long out_stride;
+    StatSet *sets;
+    Prob *probs;
+    FinDesc *fins;
+};
+
+// ---- small device helpers ----
+
+__device__ __forceinline__ void set_status(Hdr *h, unsigned st)
+{
+    atomicCAS(&h->status, 0u, st);
+}
+
+// order-preserving map of a float's bits to an unsigned integer
+__host__ __device__ __forceinline__ unsigned ord32(unsigned u)
+{
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ unsigned unord32(unsigned o)
+{
+    return (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+}
+__host__ __device__ __forceinline__ unsigned long long ord64(unsigned long long u)
+{
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ unsigned long long unord64(unsigned long long o)
+{
+    return (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+}
+
+// ---- launchers (one translation unit each) ----
+
+// stats.cu
+cudaError_t launch_convert(const void *x, int dtype, long long n, double *x64, Hdr *hdr,
+                           cudaStream_t st);
+cudaError_t launch_stats_sets(const StatSet *sets, int nsets, long long total_index,
+                              double *mu, float4 *s32, D4 *s64, cudaStream_t st);
+cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, double *mu,
+                                double *invn, double *df, double *dg, uint8_t *flat,
+                                cudaStream_t st);
+
+// plan.cu
+cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
+                        long long *band_off, Band *bands, unsigned long long *tile_prefix,
+                        long long max_bands, Hdr *hdr, cudaStream_t st);
+cudaError_t launch_family_descs(const FamilyParams &F, cudaStream_t st);
+cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int B, double ez,
+                                 unsigned flags, int fp64, const double *x64, double *mu,
+                                 float4 *s32, D4 *s64, void *keys,
+                                 double *mp, int64_t *pi, const int64_t *out_offsets,
+                                 StatSet *sets, Prob *probs, FinDesc *fins, Hdr *hdr,
+                                 cudaStream_t st);
+
+// join_fp32.cu / join_fp64.cu
+int f32_variant_count();
+bool f32_variant_info(int v, int *tile_diags, int *chunk_rows, int *threads, int *smem);
+cudaError_t launch_join_f32(int v, const Prob *probs, const Band *bands,
+                            const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                            int anchor_every, int grid, cudaStream_t st);
+int f32_blocks_per_sm(int v);
+int f64_variant_count();
+bool f64_variant_info(int v, int *tile_diags, int *chunk_rows, int *threads, int *smem);
+cudaError_t launch_join_f64(int v, const Prob *probs, const Band *bands,
+                            const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                            int anchor_every, int grid, cudaStream_t st);
+int f64_blocks_per_sm(int v);
+
+// finalize.cu
+cudaError_t launch_finalize(const FinDesc *fins, int nfin, long long max_len, int fp64,
+                            int refine, cudaStream_t st);
+
+// backward.cu
+cudaError_t launch_backward(const double *x64, long long n, int m, const double *mu,
+                            const double *invn, const uint8_t *flat, const int64_t *pi,
+                            const double *grad_mp, double *grad_x, Hdr *hdr, cudaStream_t st);
+
+}  // namespace mpgb

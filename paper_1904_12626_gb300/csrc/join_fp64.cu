@@ -1,0 +1,82 @@
+// join_fp64.cu -- all-FP64 instantiations of the diagonal-tile kernel
+// (the comparison twin of the FP32-mixed kernel: every step in FP64).
+#include "join_tile.cuh"
+
+namespace mpgb {
+namespace {
+
+template <int D, int W, int RC>
+struct V {
+    using Sh = TileShape<TraitsF64, D, W, RC>;
+    static void *fn() { return (void *)join_tile_kernel<TraitsF64, D, W, RC, 2>; }
+    static cudaError_t launch(const Prob *probs, const Band *bands,
+                              const unsigned long long *tp, Hdr *hdr, int tile_rows,
+                              int anchor_every, int grid, cudaStream_t st)
+    {
+        join_tile_kernel<TraitsF64, D, W, RC, 2><<<grid, Sh::NT, Sh::SMEM, st>>>(
+            probs, bands, tp, hdr, tile_rows, anchor_every);
+        return cudaGetLastError();
+    }
+};
+
+// variant table: {D, W, RC}
+#define MPGB_F64_VARIANTS(X) X(0, 4, 4, 128) X(1, 2, 4, 128) X(2, 8, 2, 128)
+
+}  // namespace
+
+int f64_variant_count() { return 3; }
+
+bool f64_variant_info(int v, int *tile_diags, int *chunk_rows, int *threads, int *smem)
+{
+    switch (v) {
+#define X(id, D, W, RC)                                              \
+    case id:                                                         \
+        *tile_diags = V<D, W, RC>::Sh::TD;                           \
+        *chunk_rows = RC;                                            \
+        *threads = V<D, W, RC>::Sh::NT;                              \
+        *smem = V<D, W, RC>::Sh::SMEM;                               \
+        return true;
+        MPGB_F64_VARIANTS(X)
+#undef X
+    default:
+        return false;
+    }
+}
+
+int f64_blocks_per_sm(int v)
+{
+    int n = 0;
+    switch (v) {
+#define X(id, D, W, RC)                                                                       \
+    case id:                                                                                  \
+        cudaFuncSetAttribute(V<D, W, RC>::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             V<D, W, RC>::Sh::SMEM);                                          \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, V<D, W, RC>::fn(),              \
+                                                          V<D, W, RC>::Sh::NT,                \
+                                                          V<D, W, RC>::Sh::SMEM) != cudaSuccess) \
+            n = 0;                                                                            \
+        break;
+        MPGB_F64_VARIANTS(X)
+#undef X
+    default:
+        break;
+    }
+    return n;
+}
+
+cudaError_t launch_join_f64(int v, const Prob *probs, const Band *bands,
+                            const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                            int anchor_every, int grid, cudaStream_t st)
+{
+    switch (v) {
+#define X(id, D, W, RC) \
+    case id:            \
+        return V<D, W, RC>::launch(probs, bands, tile_prefix, hdr, tile_rows, anchor_every, grid, st);
+        MPGB_F64_VARIANTS(X)
+#undef X
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mpgb

@@ -1,0 +1,291 @@
+// plan.cu -- problem descriptors and the tile work-queue.
+//
+// The distance matrix of every problem is cut into bands of `tile_diags`
+// consecutive diagonals (the paper's SCRIMP evaluates the matrix diagonal by
+// diagonal in any order, Sec. 3.3.3) and each band into tiles of `tile_rows`
+// rows.  The planner writes one Band per band and an exclusive prefix sum of
+// tiles per band; the persistent tile kernels turn a ticket into
+// (band, row tile) with a binary search over that prefix.  Everything is
+// computed on the device from device-resident descriptors, so a whole join
+// (including batches whose sizes live only on the device) can be recorded in
+// a CUDA graph.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace mpgb {
+namespace {
+
+// Exclusive scan of a[0..n) in place by one block; a[n] receives the total.
+template <typename T>
+__device__ void block_exclusive_scan(T *a, long long n)
+{
+    __shared__ T warp_tot[32];
+    __shared__ T carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < n; base += blockDim.x) {
+        const long long idx = base + tid;
+        const T v = idx < n ? a[idx] : (T)0;
+        T x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            T s = lane < nwarps ? warp_tot[lane] : (T)0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_tot[lane] = s;
+        }
+        __syncthreads();
+        const T pre = carry + (warp > 0 ? warp_tot[warp - 1] : (T)0);
+        if (idx < n) a[idx] = pre + x - v;
+        __syncthreads();
+        if (tid == blockDim.x - 1) carry = pre + x;
+        __syncthreads();
+    }
+    if (tid == 0) a[n] = carry;
+    __syncthreads();
+}
+
+__global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, int TR,
+                            long long *band_off, Band *bands, unsigned long long *tile_prefix,
+                            long long max_bands, Hdr *hdr)
+{
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+        const Prob P = probs[p];
+        long long nb = 0;
+        if (P.lR > 0 && P.lC > 0 && P.kmax >= P.kmin) nb = (P.kmax - P.kmin) / TD + 1;
+        band_off[p] = nb;
+    }
+    __syncthreads();
+    block_exclusive_scan<long long>(band_off, nprob);
+    long long total = band_off[nprob];
+    if (total > max_bands) {                   // workspace sized too small: plan nothing
+        if (threadIdx.x == 0) set_status(hdr, MP_ENOMEM);
+        total = 0;
+    }
+    if (total > 0) {
+        for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+            const Prob P = probs[p];
+            const long long off = band_off[p], nb = band_off[p + 1] - off;
+            for (long long b = 0; b < nb; ++b) {
+                const long long k0 = P.kmin + b * TD;
+                const long long rows = min(P.lR, P.lC - k0);
+                Band bd;
+                bd.prob = p;
+                bd.pad = 0;
+                bd.k0 = k0;
+                bands[off + b] = bd;
+                tile_prefix[off + b] = rows > 0 ? (unsigned long long)((rows + TR - 1) / TR) : 0ull;
+            }
+        }
+    }
+    __syncthreads();
+    block_exclusive_scan<unsigned long long>(tile_prefix, total);
+    if (threadIdx.x == 0) {
+        hdr->nbands = (int)total;
+        hdr->ntiles = tile_prefix[total];
+        hdr->ticket = 0ull;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
+                        long long *band_off, Band *bands, unsigned long long *tile_prefix,
+                        long long max_bands, Hdr *hdr, cudaStream_t st)
+{
+    plan_kernel<<<1, 1024, 0, st>>>(probs, nprob, tile_diags, tile_rows, band_off, bands,
+                                    tile_prefix, max_bands, hdr);
+    return cudaGetLastError();
+}
+
+// ---- descriptors of a self-join, an AB-join or a pan profile ----
+
+namespace {
+
+__device__ __forceinline__ long long first_diag(int m, double ez, unsigned flags)
+{
+    long long e = (long long)ceil(ez * (double)m);
+    if (flags & MP_FLAG_EXCL_INCLUSIVE) e += 1;
+    return e;
+}
+
+__global__ void family_descs_kernel(FamilyParams F)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t ksz = F.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    if (F.kind == 0 || F.kind == 2) {          // self-join / pan: one set, problem, output per m
+        const int nset = F.kind == 0 ? 1 : F.nm;
+        if (k >= nset) return;
+        const int m = F.kind == 0 ? F.m : F.ms[k];
+        const long long l = F.n - m + 1;
+        const long long sb = (long long)k * (F.n + kPad);
+        StatSet S;
+        S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.pad = 0;
+        F.sets[k] = S;
+        Prob P;
+        P.rS32 = P.cS32 = F.s32 ? F.s32 + sb : nullptr;
+        P.rS64 = P.cS64 = F.s64 + sb;
+        P.rX = P.cX = F.x64;
+        P.rMu = P.cMu = F.mu + sb;
+        P.rKey = P.cKey = F.keys + (size_t)sb * ksz;
+        P.lR = P.lC = l;
+        P.nC = F.n;
+        P.kmin = first_diag(m, F.ez, F.flags);
+        P.kmax = l - 1;
+        P.m = m;
+        P.pad = 0;
+        F.probs[k] = P;
+        FinDesc D;
+        D.key = P.rKey;
+        D.xR = D.xC = F.x64;
+        D.muR = D.muC = P.rMu;
+        D.sR = D.sC = P.rS64;
+        D.l = l; D.lC = l;
+        D.kmin = P.kmin;
+        D.pad_to = F.kind == 0 ? l : F.out_stride;
+        D.mp = F.mp_a + (long long)k * F.out_stride;
+        D.pi = F.pi_a + (long long)k * F.out_stride;
+        D.scale = (F.flags & MP_FLAG_PAN_NORMALIZE) && F.kind == 2 ? 1.0 / sqrt(2.0 * m) : 1.0;
+        D.m = m;
+        D.pad = 0;
+        F.fins[k] = D;
+        return;
+    }
+    // AB-join: sets 0 (A) and 1 (B); problem 0 = A rows x B columns (k >= 0),
+    // problem 1 = B rows x A columns (k >= 1); outputs A side then B side.
+    if (k >= 2) return;
+    const int m = F.m;
+    const long long la = F.na - m + 1, lb = F.nb - m + 1;
+    const long long sbA = 0, sbB = F.na + kPad;
+    const double *xa = F.x64, *xb = F.x64 + F.na;
+    StatSet S;
+    S.m = m; S.pad = 0;
+    if (k == 0) { S.x = xa; S.n = F.na; S.l = la; S.sbase = sbA; }
+    else { S.x = xb; S.n = F.nb; S.l = lb; S.sbase = sbB; }
+    F.sets[k] = S;
+    const bool rowA = (k == 0);
+    const long long sbR = rowA ? sbA : sbB, sbC = rowA ? sbB : sbA;
+    Prob P;
+    P.rS32 = F.s32 ? F.s32 + sbR : nullptr;
+    P.cS32 = F.s32 ? F.s32 + sbC : nullptr;
+    P.rS64 = F.s64 + sbR;
+    P.cS64 = F.s64 + sbC;
+    P.rX = rowA ? xa : xb;
+    P.cX = rowA ? xb : xa;
+    P.rMu = F.mu + sbR;
+    P.cMu = F.mu + sbC;
+    P.rKey = F.keys + (size_t)sbR * ksz;
+    P.cKey = F.keys + (size_t)sbC * ksz;
+    P.lR = rowA ? la : lb;
+    P.lC = rowA ? lb : la;
+    P.nC = rowA ? F.nb : F.na;
+    P.kmin = rowA ? 0 : 1;
+    P.kmax = P.lC - 1;
+    P.m = m;
+    P.pad = 0;
+    F.probs[k] = P;
+    FinDesc D;
+    D.key = P.rKey;
+    D.xR = P.rX; D.muR = P.rMu; D.sR = P.rS64;
+    D.xC = P.cX; D.muC = P.cMu; D.sC = P.cS64;
+    D.l = P.lR; D.lC = P.lC;
+    D.kmin = -1;
+    D.pad_to = P.lR;
+    D.mp = rowA ? F.mp_a : F.mp_b;
+    D.pi = rowA ? F.pi_a : F.pi_b;
+    D.scale = 1.0;
+    D.m = m;
+    D.pad = 0;
+    F.fins[k] = D;
+}
+
+__global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
+                                     const int32_t *__restrict__ ms, int B, double ez,
+                                     unsigned flags, int fp64, const double *x64, double *mu,
+                                     float4 *s32, D4 *s64, char *keys, double *mp,
+                                     int64_t *pi, const int64_t *__restrict__ out_offsets,
+                                     StatSet *sets, Prob *probs, FinDesc *fins, Hdr *hdr)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const size_t ksz = fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    const long long o0 = offsets[0];
+    const long long off = offsets[b] - o0;
+    const long long n = offsets[b + 1] - offsets[b];
+    const int m = ms[b];
+    long long l = n - m + 1;
+    if (m < 4 || n < 0) {
+        set_status(hdr, MP_EINVAL);
+        l = 0;
+    }
+    if (l < 0) l = 0;
+    const long long cap = out_offsets[b + 1] - out_offsets[b];
+    if (l > cap) {
+        set_status(hdr, MP_EINVAL);
+        l = 0;
+    }
+    const long long sb = off + (long long)b * kPad;
+    StatSet S;
+    S.x = x64 + off; S.n = n; S.l = l; S.sbase = sb; S.m = m; S.pad = 0;
+    sets[b] = S;
+    Prob P;
+    P.rS32 = P.cS32 = s32 ? s32 + sb : nullptr;
+    P.rS64 = P.cS64 = s64 + sb;
+    P.rX = P.cX = x64 + off;
+    P.rMu = P.cMu = mu + sb;
+    P.rKey = P.cKey = keys + (size_t)sb * ksz;
+    P.lR = P.lC = l;
+    P.nC = n;
+    P.kmin = first_diag(m, ez, flags);
+    P.kmax = l - 1;
+    P.m = m;
+    P.pad = 0;
+    probs[b] = P;
+    FinDesc D;
+    D.key = P.rKey;
+    D.xR = D.xC = P.rX;
+    D.muR = D.muC = P.rMu;
+    D.sR = D.sC = P.rS64;
+    D.l = l; D.lC = l;
+    D.kmin = P.kmin;
+    D.pad_to = l;
+    D.mp = mp + out_offsets[b];
+    D.pi = (long long *)pi + out_offsets[b];
+    D.scale = 1.0;
+    D.m = m;
+    D.pad = 0;
+    fins[b] = D;
+}
+
+}  // namespace
+
+cudaError_t launch_family_descs(const FamilyParams &F, cudaStream_t st)
+{
+    family_descs_kernel<<<1, 256, 0, st>>>(F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int B, double ez,
+                                 unsigned flags, int fp64, const double *x64, double *mu,
+                                 float4 *s32, D4 *s64, void *keys, double *mp, int64_t *pi,
+                                 const int64_t *out_offsets, StatSet *sets, Prob *probs,
+                                 FinDesc *fins, Hdr *hdr, cudaStream_t st)
+{
+    const int threads = 256;
+    batched_descs_kernel<<<(B + threads - 1) / threads, threads, 0, st>>>(
+        offsets, ms, B, ez, flags, fp64, x64, mu, s32, s64, (char *)keys, mp, pi, out_offsets,
+        sets, probs, fins, hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace mpgb
