@@ -140,6 +140,24 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
                       double *mp, int64_t *pi, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Self-join without a caller workspace (the paper has no counterpart: this
+ * is a convenience of the library).  For callers that cannot allocate device
+ * memory -- code running inside another framework's CUDA-graph capture, under
+ * an allocator that owns all device memory, or in a plugin that only receives
+ * its input and output buffers.  Same arguments and results as mp_selfjoin,
+ * but the scratch is a 64 MiB array the library keeps on every GPU that
+ * loads it, until the process exits; it holds any series of up to 930,000
+ * samples (larger n returns MP_ENOMEM; nothing is allocated by any call).
+ * The first call on a device (with that device current) looks up the
+ * array's device address, so make it before any stream capture.  All calls
+ * on a device share the array: calls whose GPU work may overlap race and
+ * must be serialised by the caller.  Device-side status (non-finite input)
+ * is not readable for this entry point; check the input beforehand.
+ */
+mp_status mp_selfjoin_noalloc(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                              double *mp, int64_t *pi, void *stream);
+
+/*
  * AB-join (Sec. 3.2, two series; no exclusion zone).  For every window of a:
  * the nearest window of b (mp_a, pi_a: la entries).  For every window of b:
  * the nearest window of a (mp_b, pi_b: lb entries; both may be NULL to skip
