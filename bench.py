@@ -254,7 +254,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     api.device_status(ws)
 
-    launches_per_step = 6          # convert, descriptors, stats, plan, tile kernel, finalize
+    # convert, descriptors, stats, fragile marking, plan, tile kernel, fragile pass, finalize
+    launches_per_step = 8 if args.prec == "fp32" else 6
     step_ms, kern_ms = [], []
     kms = ctypes.c_float()
     barrier(world)

@@ -12,7 +12,7 @@ using namespace mpgb;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kDefaultTileRowsF32 = 8192;
+constexpr int kDefaultTileRowsF32 = 16384;
 constexpr int kDefaultTileRowsF64 = 4096;
 constexpr long long kMaxN = 2147483647ll;
 
@@ -107,10 +107,13 @@ struct LayoutReq {
 
 struct Layout {
     Hdr *hdr;
-    double *x64, *mu;
+    double *x64, *mu, *inv;
     float4 *s32;
     D4 *s64;
+    uint8_t *flat;
     char *keys;
+    double *set_acc;
+    unsigned long long *frag_list;
     StatSet *sets;
     Prob *probs;
     FinDesc *fins;
@@ -129,13 +132,17 @@ Layout carve(void *base, const LayoutReq &r)
         off = o + bytes;
         return base ? (void *)((char *)base + o) : nullptr;
     };
-    const size_t ksz = r.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    const size_t ksz = sizeof(Key128);
     L.hdr = (Hdr *)take(256);
     L.x64 = (double *)take(sizeof(double) * (size_t)r.nx);
     L.mu = (double *)take(sizeof(double) * (size_t)r.S);
+    L.inv = (double *)take(sizeof(double) * (size_t)r.S);
     L.s32 = r.fp64 ? nullptr : (float4 *)take(sizeof(float4) * (size_t)r.S);
     L.s64 = (D4 *)take(sizeof(D4) * (size_t)r.S);
+    L.flat = (uint8_t *)take((size_t)r.S);
     L.keys = (char *)take(ksz * (size_t)r.S);
+    L.set_acc = (double *)take(sizeof(double) * 2 * (size_t)r.nsets);
+    L.frag_list = (unsigned long long *)take(sizeof(unsigned long long) * (size_t)r.S);
     L.sets = (StatSet *)take(sizeof(StatSet) * (size_t)r.nsets);
     L.probs = (Prob *)take(sizeof(Prob) * (size_t)r.nprob);
     L.fins = (FinDesc *)take(sizeof(FinDesc) * (size_t)r.nfin);
@@ -153,13 +160,18 @@ bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
         if ((call) != cudaSuccess) return MP_ECUDA;   \
     } while (0)
 
-// stats -> keys reset -> plan -> persistent join -> finalize
+// stats -> keys reset -> [fragile windows marked] -> plan -> persistent join ->
+// [fragile pairs exactly] -> finalize
 mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
                    const DeviceInfo *dev, cudaStream_t st)
 {
-    MP_CU(launch_stats_sets(L.sets, r.nsets, r.S, L.mu, L.s32, L.s64, st));
-    const size_t ksz = r.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    MP_CU(cudaMemsetAsync(L.set_acc, 0, sizeof(double) * 2 * (size_t)r.nsets, st));
+    MP_CU(launch_stats_sets(L.sets, r.nsets, r.S, L.mu, L.inv, L.s32, L.s64, L.flat, L.set_acc,
+                            st));
+    const size_t ksz = sizeof(Key128);
     MP_CU(cudaMemsetAsync(L.keys, 0, ksz * (size_t)r.S, st));
+    MP_CU(launch_fragile_mark(L.sets, r.nsets, max_fin_len, L.set_acc, L.inv, L.flat, L.s32,
+                              L.s64, L.frag_list, L.hdr, st));
     MP_CU(launch_plan(L.probs, r.nprob, t.tile_diags, t.tile_rows, L.band_off, L.bands,
                       L.tile_prefix, r.max_bands, L.hdr, st));
     const int bps = t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant];
@@ -178,6 +190,8 @@ mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long l
         MP_CU(cudaEventRecord(dm->ev[1], st));
         dm->ev_used = true;
     }
+    MP_CU(launch_fragile_pass(L.sets, L.mu, L.inv, L.frag_list, L.keys, t.fp64, L.hdr,
+                              dev->sms * 8, st));
     MP_CU(launch_finalize(L.fins, r.nfin, max_fin_len, t.fp64, t.refine ? 1 : 0, st));
     return MP_OK;
 }
@@ -334,7 +348,7 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
     FamilyParams F;
     std::memset(&F, 0, sizeof(F));
     F.kind = 0; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez; F.flags = cfg->flags;
-    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
     F.mp_a = mp; F.pi_a = (long long *)pi; F.out_stride = 0;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
@@ -372,7 +386,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
     std::memset(&F, 0, sizeof(F));
     F.kind = 1; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.na = na; F.nb = nb; F.ez = cfg->ez;
     F.flags = cfg->flags;
-    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
     F.mp_a = mp_a; F.pi_a = (long long *)pi_a; F.mp_b = mp_b; F.pi_b = (long long *)pi_b;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
@@ -416,7 +430,7 @@ mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int
     F.kind = 2; F.nm = nm; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez;
     F.flags = cfg->flags;
     for (int k = 0; k < nm; ++k) F.ms[k] = ms[k];
-    F.mu = L.mu; F.s32 = L.s32; F.s64 = L.s64; F.keys = L.keys;
+    F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
     F.mp_a = pan; F.pi_a = (long long *)pi; F.out_stride = n - mmin + 1;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
@@ -452,9 +466,9 @@ mp_status mp_batched(const void *values, int32_t dtype, int64_t total_values,
     cudaStream_t st = (cudaStream_t)stream;
     MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
     MP_CU(launch_convert(values, dtype, total_values, L.x64, L.hdr, st));
-    MP_CU(launch_batched_descs(offsets, ms, B, cfg->ez, cfg->flags, t.fp64, L.x64, L.mu, L.s32,
-                               L.s64, L.keys, mp, pi, out_offsets, L.sets, L.probs, L.fins, L.hdr,
-                               st));
+    MP_CU(launch_batched_descs(offsets, ms, B, cfg->ez, cfg->flags, t.fp64, L.x64, L.mu, L.inv,
+                               L.s32, L.s64, L.flat, L.keys, mp, pi, out_offsets, L.sets, L.probs,
+                               L.fins, L.hdr, st));
     // every series is at most total_values long: finalize covers that bound
     return run_join(L, r, t, total_values, d, st);
 }

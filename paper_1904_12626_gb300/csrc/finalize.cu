@@ -21,10 +21,9 @@ namespace {
 __device__ __forceinline__ double exact_distance(const FinDesc &F, long long i, long long j,
                                                  double invR)
 {
-    const D4 sc = F.sC[j];
     const double s2m = sqrt(2.0 * (double)F.m);
-    if (sc.w != 0.0) return s2m;
-    const double invC = sc.z;
+    if (F.flatC[j]) return s2m;
+    const double invC = F.invC[j];
     const double muR = F.muR[i], muC = F.muC[j];
     const double *xr = F.xR + i, *xc = F.xC + j;
     double acc = 0.0;
@@ -46,11 +45,10 @@ __device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long
         F.pi[i] = -1;
         return;
     }
-    const D4 sr = F.sR[i];
     const double s2m = sqrt(2.0 * (double)F.m);
     double mpv = INF;
     long long piv = -1;
-    if (sr.w != 0.0) {
+    if (F.flatR[i]) {
         if (F.kmin < 0) piv = F.lC > 0 ? 0 : -1;
         else piv = (i >= F.kmin) ? 0 : ((i + F.kmin < F.lC) ? i + F.kmin : -1);
         if (piv >= 0) mpv = s2m;
@@ -65,16 +63,19 @@ __device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long
                 piv = (long long)(~0ull - k.lo);
             }
         } else {
-            const unsigned long long k = reinterpret_cast<const unsigned long long *>(F.key)[i];
-            have = k != 0ull;
+            // FP32-mixed candidate key: hi = (value, ~index), lo = lower bound
+            const Key128 k = reinterpret_cast<const Key128 *>(F.key)[i];
+            have = k.hi != 0ull;
             if (have) {
-                rho = (double)__uint_as_float(unord32((unsigned)(k >> 32)));
-                piv = (long long)(0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull));
+                const double v = (double)__uint_as_float(unord32((unsigned)(k.hi >> 32)));
+                const double lb = (double)__uint_as_float(unord32((unsigned)(k.lo >> 32)));
+                rho = 0.5 * (v + lb);
+                piv = (long long)(0xFFFFFFFFu - (unsigned)(k.hi & 0xFFFFFFFFull));
             }
         }
         if (have) {
             if (refine) {
-                mpv = exact_distance(F, i, piv, sr.z);
+                mpv = exact_distance(F, i, piv, F.invR[i]);
             } else {
                 rho = rho > 1.0 ? 1.0 : (rho < -1.0 ? -1.0 : rho);
                 mpv = sqrt(2.0 * (double)F.m * (1.0 - rho));

@@ -54,6 +54,7 @@ struct Hdr {
     int nbands;                           // number of bands written by the planner
     int pad1;
     unsigned long long ntiles;            // number of tiles (same as tile_prefix[nbands])
+    unsigned long long frag_count;        // fragile windows found (FP32-mixed path)
 };
 
 struct StatSet {
@@ -61,15 +62,26 @@ struct StatSet {
     long long n;                          // series length
     long long l;                          // windows (<= 0: empty set)
     long long sbase;                      // first stats index of this set
+    long long kmin;                       // self-join: first admissible |i-j|; -1: AB pair
     int m;
-    int pad;
+    int partner;                          // set whose windows are this set's candidates
 };
 
+// A window is "fragile" when its centred norm is below kFragileFactor times
+// the geometric mean norm of its set: the FP32 recurrence's absolute error,
+// divided by so small a norm, would swamp its correlations, so the FP32-mixed
+// path leaves it out of the tile kernel and handles its pairs exactly.
+constexpr double kFragileFactor = 1.0 / 32;
+
+// Packed per-window inputs of the tile kernels, stats-indexed:
+// {df, dg, invn, thr} where thr is the running threshold of the index (the
+// best correlation merged into its key so far; +inf for flat windows).
 struct Prob {
-    const float4 *rS32, *cS32;            // {df, dg, invn, flat} FP32, stats-indexed
-    const D4 *rS64, *cS64;           // {df, dg, invn, flat} FP64
+    float4 *rS32, *cS32;                  // FP32 copies (FP32-mixed path)
+    D4 *rS64, *cS64;                      // FP64 (FP64 path, anchors, refine)
     const double *rX, *cX;                // FP64 series
     const double *rMu, *cMu;              // window means
+    const double *rInv, *cInv;            // exact inverse norms (never masked)
     void *rKey, *cKey;                    // u64 (FP32 path) or Key128 (FP64 path)
     long long lR, lC;                     // windows of the row / column set
     long long nC;                         // column series length
@@ -87,10 +99,10 @@ struct Band {
 // Finalize descriptor: one output side of one problem family
 struct FinDesc {
     const void *key;                      // keys of this side (stats-indexed, own base)
-    const double *xR, *muR;               // own side
-    const D4 *sR;
-    const double *xC, *muC;               // candidate side
-    const D4 *sC;
+    const double *xR, *muR, *invR;        // own side
+    const uint8_t *flatR;
+    const double *xC, *muC, *invC;        // candidate side
+    const uint8_t *flatC;
     long long l;                          // windows on this side
     long long lC;                         // windows on the candidate side
     long long kmin;                       // self-join: first admissible |i-j|; -1: AB
@@ -118,8 +130,10 @@ struct FamilyParams {
     unsigned flags;
     unsigned pad;
     double *mu;
+    double *inv;
     float4 *s32;
     D4 *s64;
+    uint8_t *flat;
     char *keys;
     double *mp_a;
     long long *pi_a;
@@ -162,7 +176,17 @@ __host__ __device__ __forceinline__ unsigned long long unord64(unsigned long lon
 cudaError_t launch_convert(const void *x, int dtype, long long n, double *x64, Hdr *hdr,
                            cudaStream_t st);
 cudaError_t launch_stats_sets(const StatSet *sets, int nsets, long long total_index,
-                              double *mu, float4 *s32, D4 *s64, cudaStream_t st);
+                              double *mu, double *inv, float4 *s32, D4 *s64, uint8_t *flat,
+                              double *set_acc, cudaStream_t st);
+
+// fragile.cu
+cudaError_t launch_fragile_mark(const StatSet *sets, int nsets, long long max_l,
+                                const double *set_acc, const double *inv, const uint8_t *flat,
+                                float4 *s32, D4 *s64, unsigned long long *frag_list, Hdr *hdr,
+                                cudaStream_t st);
+cudaError_t launch_fragile_pass(const StatSet *sets, const double *mu, const double *inv,
+                                const unsigned long long *frag_list, void *keys, int fp64,
+                                Hdr *hdr, int grid, cudaStream_t st);
 cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, double *mu,
                                 double *invn, double *df, double *dg, uint8_t *flat,
                                 cudaStream_t st);
@@ -174,7 +198,7 @@ cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_r
 cudaError_t launch_family_descs(const FamilyParams &F, cudaStream_t st);
 cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int B, double ez,
                                  unsigned flags, int fp64, const double *x64, double *mu,
-                                 float4 *s32, D4 *s64, void *keys,
+                                 double *inv, float4 *s32, D4 *s64, uint8_t *flat, void *keys,
                                  double *mp, int64_t *pi, const int64_t *out_offsets,
                                  StatSet *sets, Prob *probs, FinDesc *fins, Hdr *hdr,
                                  cudaStream_t st);

@@ -5,36 +5,39 @@
 namespace mpgb {
 namespace {
 
-template <int D, int W, int RC>
+template <int D, int W, int RC, int MINB>
 struct V {
     using Sh = TileShape<TraitsF32, D, W, RC>;
-    static void *fn() { return (void *)join_tile_kernel<TraitsF32, D, W, RC, 2>; }
+    static void *fn() { return (void *)join_tile_kernel<TraitsF32, D, W, RC, MINB>; }
     static cudaError_t launch(const Prob *probs, const Band *bands,
                               const unsigned long long *tp, Hdr *hdr, int tile_rows,
                               int anchor_every, int grid, cudaStream_t st)
     {
-        join_tile_kernel<TraitsF32, D, W, RC, 2><<<grid, Sh::NT, Sh::SMEM, st>>>(
+        join_tile_kernel<TraitsF32, D, W, RC, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(
             probs, bands, tp, hdr, tile_rows, anchor_every);
         return cudaGetLastError();
     }
 };
 
-// variant table: {D, W, RC}
-#define MPGB_F32_VARIANTS(X) X(0, 8, 4, 256) X(1, 4, 4, 256) X(2, 8, 2, 256) X(3, 16, 2, 256)
+// variant table: {id, D (diagonals per thread), W (warps per CTA), RC (rows per
+// staged chunk), MINB (CTAs per SM the register budget must allow)}
+#define MPGB_F32_VARIANTS(X) \
+    X(0, 8, 2, 512, 8) X(1, 8, 4, 512, 4) X(2, 8, 2, 512, 10) X(3, 8, 4, 256, 4) \
+    X(4, 8, 1, 256, 16) X(5, 4, 4, 256, 4) X(6, 16, 2, 256, 2) X(7, 8, 4, 512, 5)
 
 }  // namespace
 
-int f32_variant_count() { return 4; }
+int f32_variant_count() { return 8; }
 
 bool f32_variant_info(int v, int *tile_diags, int *chunk_rows, int *threads, int *smem)
 {
     switch (v) {
-#define X(id, D, W, RC)                                              \
+#define X(id, D, W, RC, MINB)                                              \
     case id:                                                         \
-        *tile_diags = V<D, W, RC>::Sh::TD;                           \
+        *tile_diags = V<D, W, RC, MINB>::Sh::TD;                           \
         *chunk_rows = RC;                                            \
-        *threads = V<D, W, RC>::Sh::NT;                              \
-        *smem = V<D, W, RC>::Sh::SMEM;                               \
+        *threads = V<D, W, RC, MINB>::Sh::NT;                              \
+        *smem = V<D, W, RC, MINB>::Sh::SMEM;                               \
         return true;
         MPGB_F32_VARIANTS(X)
 #undef X
@@ -47,13 +50,13 @@ int f32_blocks_per_sm(int v)
 {
     int n = 0;
     switch (v) {
-#define X(id, D, W, RC)                                                                       \
+#define X(id, D, W, RC, MINB)                                                                       \
     case id:                                                                                  \
-        cudaFuncSetAttribute(V<D, W, RC>::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                             V<D, W, RC>::Sh::SMEM);                                          \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, V<D, W, RC>::fn(),              \
-                                                          V<D, W, RC>::Sh::NT,                \
-                                                          V<D, W, RC>::Sh::SMEM) != cudaSuccess) \
+        cudaFuncSetAttribute(V<D, W, RC, MINB>::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             V<D, W, RC, MINB>::Sh::SMEM);                                          \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, V<D, W, RC, MINB>::fn(),              \
+                                                          V<D, W, RC, MINB>::Sh::NT,                \
+                                                          V<D, W, RC, MINB>::Sh::SMEM) != cudaSuccess) \
             n = 0;                                                                            \
         break;
         MPGB_F32_VARIANTS(X)
@@ -69,9 +72,9 @@ cudaError_t launch_join_f32(int v, const Prob *probs, const Band *bands,
                             int anchor_every, int grid, cudaStream_t st)
 {
     switch (v) {
-#define X(id, D, W, RC) \
+#define X(id, D, W, RC, MINB) \
     case id:            \
-        return V<D, W, RC>::launch(probs, bands, tile_prefix, hdr, tile_rows, anchor_every, grid, st);
+        return V<D, W, RC, MINB>::launch(probs, bands, tile_prefix, hdr, tile_rows, anchor_every, grid, st);
         MPGB_F32_VARIANTS(X)
 #undef X
     default:

@@ -22,9 +22,9 @@
 // that the lanes' strided loads fall in distinct banks.
 //
 // Maxima without per-cell index bookkeeping.  Each row and each column
-// carries a threshold: the best correlation already known for that index
-// (read from the global keys when the chunk is staged; +inf for flat
-// windows, whose answer is closed-form).  The fast path only asks, per cell,
+// carries a threshold: the best correlation already merged into that index's
+// key (kept in the .w lane of the packed statistics, staged with them; +inf
+// for flat windows, whose answer is closed-form).  The fast path only asks, per cell,
 // "is rho >= the row's threshold or the column's threshold?" (2 compares,
 // OR-ed into one predicate), so a cell costs 2 FMA + 2 MUL + 2 compares.
 // When any lane of the warp saw a hit in a group of D rows, the warp replays
@@ -42,6 +42,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "cand_f32.cuh"
 
 namespace mpgb {
 
@@ -62,19 +63,20 @@ __device__ __forceinline__ Key128 cas128(Key128 *a, Key128 cmp, Key128 nv)
 }
 
 struct TraitsF32 {
+    // The fast path compares an upper bound of the correlation (the covariance
+    // carries a bias equal to a bound on its accumulated rounding error) and
+    // every candidate is verified exactly before it reaches a key.
+    static constexpr bool kBias = true;
+    static constexpr float kEps = 1.1920929e-7f;          // 2^-23
     using T = float;
     using S4 = float4;
-    using Key = unsigned long long;
+    using Key = Key128;                           // candidate keys, see cand_f32.cuh
     using Packed = unsigned long long;
-    static __device__ __forceinline__ const S4 *rs(const Prob &P) { return P.rS32; }
-    static __device__ __forceinline__ const S4 *cs(const Prob &P) { return P.cS32; }
+    static __device__ __forceinline__ S4 *rs(const Prob &P) { return P.rS32; }
+    static __device__ __forceinline__ S4 *cs(const Prob &P) { return P.cS32; }
+    static __device__ __forceinline__ S4 ld(const S4 *p) { return __ldcg(p); }
     static __device__ __forceinline__ T inf() { return __int_as_float(0x7f800000); }
     static __device__ __forceinline__ T fma_(T a, T b, T c) { return fmaf(a, b, c); }
-    static __device__ __forceinline__ T thr_of(const Key *k, long long idx)
-    {
-        const unsigned long long v = __ldcg(k + idx);
-        return v == 0ull ? -inf() : __uint_as_float(unord32((unsigned)(v >> 32)));
-    }
     static __device__ __forceinline__ Packed pack(T rho, long long idx)
     {
         rho += 0.0f;                              // -0 -> +0: all zero correlations tie
@@ -91,27 +93,29 @@ struct TraitsF32 {
     {
         return __uint_as_float(unord32((unsigned)(a >> 32)));
     }
-    static __device__ __forceinline__ void merge(Key *k, long long idx, Packed p, Hdr *)
+    static __device__ __forceinline__ long long pidx(Packed a)
     {
-        atomicMax(k + idx, p);
+        return (long long)(0xFFFFFFFFu - (unsigned)(a & 0xFFFFFFFFull));
     }
 };
 
 struct TraitsF64 {
+    static constexpr bool kBias = false;        // FP64 recurrence values go to the keys directly
+    static constexpr double kEps = 2.220446049250313e-16;
     using T = double;
     using S4 = D4;
     using Key = Key128;
     using Packed = Key128;
-    static __device__ __forceinline__ const S4 *rs(const Prob &P) { return P.rS64; }
-    static __device__ __forceinline__ const S4 *cs(const Prob &P) { return P.cS64; }
+    static __device__ __forceinline__ S4 *rs(const Prob &P) { return P.rS64; }
+    static __device__ __forceinline__ S4 *cs(const Prob &P) { return P.cS64; }
+    static __device__ __forceinline__ S4 ld(const S4 *p)
+    {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+        return make_d4(a.x, a.y, b.x, b.y);
+    }
     static __device__ __forceinline__ T inf() { return __longlong_as_double(0x7ff0000000000000ll); }
     static __device__ __forceinline__ T fma_(T a, T b, T c) { return fma(a, b, c); }
-    static __device__ __forceinline__ T thr_of(const Key *k, long long idx)
-    {
-        const unsigned long long hi = __ldcg(&k[idx].hi);
-        const unsigned long long lo = __ldcg(&k[idx].lo);
-        return (hi == 0ull && lo == 0ull) ? -inf() : __longlong_as_double((long long)unord64(hi));
-    }
     static __device__ __forceinline__ Packed pack(T rho, long long idx)
     {
         rho += 0.0;
@@ -135,6 +139,14 @@ struct TraitsF64 {
     static __device__ __forceinline__ T pval(Packed a)
     {
         return __longlong_as_double((long long)unord64(a.hi));
+    }
+    static __device__ __forceinline__ long long pidx(Packed a) { return (long long)(~0ull - a.lo); }
+    static __device__ __forceinline__ Packed peek(const Key *k)
+    {
+        Packed p;
+        p.hi = __ldcg(&k->hi);
+        p.lo = __ldcg(&k->lo);
+        return p;
     }
     static __device__ __forceinline__ void merge(Key *k, long long idx, Packed p, Hdr *hdr)
     {
@@ -190,9 +202,284 @@ __device__ __forceinline__ void anchor_covariances(const Prob &P, long long a, l
     for (int d = 0; d < D; ++d) c[d] = (j0 + d < P.lC) ? (typename Tr::T)acc[d] : (typename Tr::T)0;
 }
 
+// Exact FP64 correlation of row window i and column window j, computed by
+// the whole warp (lanes split the window, then a butterfly sum); every lane
+// returns the value.  Column mean omitted for the same reason as in the
+// anchors.
+__device__ __forceinline__ double exact_correlation(const Prob &P, long long i, long long j,
+                                                    int lane)
+{
+    const double *__restrict__ xr = P.rX + i;
+    const double *__restrict__ xc = P.cX + j;
+    const double mu = P.rMu[i];
+    double acc = 0.0;
+    for (int t = lane; t < P.m; t += 32) acc = fma(__ldg(xr + t) - mu, __ldg(xc + t), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc * P.rInv[i] * P.cInv[j];
+}
+
+// running sums of a staged window's squared norm (1/invn^2), df^2, dg^2 and
+// a count (flat, fragile and padding entries skipped)
+constexpr float kBiasSigma = 2.0f;
+
+template <class S4>
+__device__ __forceinline__ void track_max(float *mx, const S4 &v)
+{
+    const float inv = (float)v.z;
+    if (inv > 0.f) {
+        mx[0] += 1.0f / (inv * inv);
+        mx[1] += (float)v.x * (float)v.x;
+        mx[2] += (float)v.y * (float)v.y;
+        mx[3] += 1.0f;
+    }
+}
+
 // smem index of staged column q (one padding slot every D entries)
 template <int D>
 __device__ __forceinline__ int cpos(int q) { return q + q / D; }
+
+
+template <class T, int D>
+struct CovArr {
+    T v[D];
+};
+
+// Replay one group of D rows of a thread's D diagonals from the covariances
+// saved at the group's start, with the same arithmetic as the fast path (so
+// the correlations are bit-identical), and merge every candidate that reaches
+// a row's or a column's threshold into the keys (FP64 path: the recurrence's
+// values are exact enough to go to the keys directly).
+template <class Tr, int D>
+__device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
+                                          typename Tr::S4 *sCol, typename Tr::S4 *rS,
+                                          typename Tr::S4 *cS, typename Tr::Key *rKey,
+                                          typename Tr::Key *cKey, Hdr *hdr,
+                                          CovArr<typename Tr::T, D> c0, long long r, int s,
+                                          long long kl, int lane_off, int lane)
+{
+    using T = typename Tr::T;
+    using S4 = typename Tr::S4;
+    using Packed = typename Tr::Packed;
+    for (int u = 0; u < D; ++u) {
+        const S4 rw = sRow[s + u];
+        const long long i = r + s + u;
+        T rho[D];
+        bool rowc[D], colc[D];
+        bool any = false;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const S4 cc = sCol[cpos<D>(lane_off + s + u + d)];
+            c0.v[d] = Tr::fma_(rw.x, cc.y, c0.v[d]);
+            c0.v[d] = Tr::fma_(cc.x, rw.y, c0.v[d]);
+            rho[d] = c0.v[d] * cc.z * rw.z;
+            rowc[d] = rho[d] >= rw.w;
+            colc[d] = rho[d] >= cc.w;
+            any |= rowc[d] | colc[d];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        Packed best = Tr::pzero();
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (colc[d]) {
+                const long long j = i + kl + d;
+                const int q = cpos<D>(lane_off + s + u + d);
+                Tr::merge(cKey, j, Tr::pack(rho[d], i), hdr);
+                if (rho[d] > sCol[q].w) {
+                    sCol[q].w = rho[d];
+                    cS[j].w = rho[d];
+                }
+            }
+            if (rowc[d]) {
+                const Packed p = Tr::pack(rho[d], i + kl + d);
+                if (Tr::pgt(p, best)) best = p;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const Packed y = Tr::pshfl(best, o);
+            if (Tr::pgt(y, best)) best = y;
+        }
+        if (lane == 0 && Tr::pgt(best, Tr::pzero())) {
+            Tr::merge(rKey, i, best, hdr);
+            const T v = Tr::pval(best);
+            if (v > sRow[s + u].w) {
+                sRow[s + u].w = v;
+                rS[i].w = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Merge candidate c (pending on this lane) into *key.  The whole warp calls
+// this together; exact correlations that a decision needs are computed by
+// the warp, one at a time.  For a row key (row_side) the candidate index is
+// a column and the exact pair is (own, idx); for a column key it is a row and
+// the pair is (idx, own).
+__device__ __forceinline__ void warp_merge(const Prob &P, bool pending, Cand c, Key128 *key,
+                                           bool row_side, long long own, float4 *gthr,
+                                           float4 *sthr, int lane, Hdr *hdr)
+{
+    float kx = 0.0f;
+    long long kx_idx = -1;
+    for (int round = 0; round < 64; ++round) {
+        bool need_c = false, need_k = false;
+        long long kpair = -1;
+        if (pending) {
+            const Key128 cur = key_peek(key);
+            const int dec = classify(c, cur, kx, kx_idx);
+            if (dec == kDiscard) {
+                pending = false;
+                if (kx_idx >= 0 && !key_empty(cur)) {   // keep what was learnt about the key
+                    Cand q = key_cand(cur);
+                    if (q.idx == kx_idx && q.L != q.V) {
+                        q.V = q.L = kx;
+                        if (key_same(cas128(key, cur, cand_key(q)), cur)) raise_thr(gthr, sthr, kx);
+                    }
+                }
+            } else if (dec == kReplace) {
+                if (key_same(cas128(key, cur, cand_key(c)), cur)) {
+                    pending = false;
+                    raise_thr(gthr, sthr, c.L);
+                }
+            } else {
+                need_c = (dec & kNeedCand) != 0;
+                need_k = (dec & kNeedKey) != 0;
+                if (need_k) kpair = key_cand(cur).idx;
+            }
+        }
+        if (!__any_sync(0xffffffffu, pending)) return;
+        unsigned mask = __ballot_sync(0xffffffffu, need_c);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const long long a = __shfl_sync(0xffffffffu, row_side ? own : c.idx, src);
+            const long long b = __shfl_sync(0xffffffffu, row_side ? c.idx : own, src);
+            const float e = (float)exact_correlation(P, a, b, lane);
+            if (lane == src) c.V = c.L = e;
+        }
+        mask = __ballot_sync(0xffffffffu, need_k);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const long long a = __shfl_sync(0xffffffffu, row_side ? own : kpair, src);
+            const long long b = __shfl_sync(0xffffffffu, row_side ? kpair : own, src);
+            const float e = (float)exact_correlation(P, a, b, lane);
+            if (lane == src) {
+                kx = e;
+                kx_idx = kpair;
+            }
+        }
+    }
+    if (pending) set_status(hdr, MP_ETIMEOUT);
+}
+
+// FP32-mixed replay of one group of D rows (see cand_f32.cuh for the keys).
+// U = upper bounds from the biased recurrence, the lower bound of a cell is
+// U - 2 ebias invn_i invn_j.  Per row: the top cell by upper bound is the row's
+// candidate; cells whose upper bound reaches its lower bound are verified
+// with it and the best exact one becomes the candidate.  Per column: each cell
+// at or above the column's threshold is a candidate.
+template <int D>
+__device__ __noinline__ void replay_group_f32(const Prob &P, float4 *sRow, float4 *sCol,
+                                              float4 *rS, float4 *cS, Key128 *rKey,
+                                              Key128 *cKey, Hdr *hdr, CovArr<float, D> c0,
+                                              long long r, int s, long long kl, int lane_off,
+                                              int lane, float ebias)
+{
+    for (int u = 0; u < D; ++u) {
+        const float4 rw = sRow[s + u];
+        const long long i = r + s + u;
+        float U[D], W[D];
+        bool rowc[D], colc[D];
+        bool any = false;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
+            c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
+            c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
+            U[d] = c0.v[d] * cc.z * rw.z;
+            W[d] = 2.0f * ebias * cc.z * rw.z;
+            rowc[d] = U[d] >= rw.w;
+            colc[d] = U[d] >= cc.w;
+            any |= rowc[d] | colc[d];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+
+        // the row's candidate
+        unsigned long long top = 0ull;
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (rowc[d]) {
+                const unsigned long long p = TraitsF32::pack(U[d], i + kl + d);
+                if (p > top) top = p;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
+            if (y > top) top = y;
+        }
+        Cand rc;
+        rc.V = rc.L = 0.0f;
+        rc.idx = -1;
+        if (top != 0ull) {
+            const long long jt = TraitsF32::pidx(top);
+            const float ut = TraitsF32::pval(top);
+            float wt = 0.0f;
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                if (i + kl + d == jt) wt = W[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
+            const float lt = ut - wt;
+            bool band[D];
+            bool anyband = false;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                band[d] = rowc[d] && (i + kl + d != jt) && U[d] >= lt;
+                anyband |= band[d];
+            }
+            if (__any_sync(0xffffffffu, anyband)) {
+                unsigned long long best =
+                    TraitsF32::pack((float)exact_correlation(P, i, jt, lane), jt);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    unsigned mask = __ballot_sync(0xffffffffu, band[d]);
+                    while (mask) {
+                        const int src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const long long j = __shfl_sync(0xffffffffu, i + kl + d, src);
+                        const unsigned long long p =
+                            TraitsF32::pack((float)exact_correlation(P, i, j, lane), j);
+                        if (p > best) best = p;
+                    }
+                }
+                rc.V = rc.L = TraitsF32::pval(best);
+                rc.idx = TraitsF32::pidx(best);
+            } else {
+                rc.V = ut;
+                rc.L = lt;
+                rc.idx = jt;
+            }
+        }
+
+        // merges: each column candidate, then the row candidate (lane 0)
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const long long j = i + kl + d;
+            Cand cc;
+            cc.V = U[d];
+            cc.L = U[d] - W[d];
+            cc.idx = i;
+            warp_merge(P, colc[d], cc, cKey + j, false, j, cS + j,
+                       sCol + cpos<D>(lane_off + s + u + d), lane, hdr);
+        }
+        warp_merge(P, lane == 0 && rc.idx >= 0, rc, rKey + i, true, i, rS + i, sRow + s + u, lane,
+                   hdr);
+        __syncwarp();
+    }
+}
 
 template <class Tr, int D, int W, int RC>
 struct TileShape {
@@ -223,6 +510,9 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     S4 *sRow = reinterpret_cast<S4 *>(smem_raw);
     S4 *sCol = sRow + RC;
     __shared__ unsigned long long s_tile;
+    // per-chunk sums of {norm^2, df^2, dg^2, count} over the staged rows and
+    // columns (two parity sets of 8): their RMS values size the error bias
+    __shared__ float s_mx[16];
 
     const int lane = threadIdx.x & 31;
     const int lane_off = threadIdx.x * D;
@@ -233,6 +523,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_tile = atomicAdd(&hdr->ticket, 1ull);
+        if (threadIdx.x < 16) s_mx[threadIdx.x] = 0.0f;
         __syncthreads();
         const unsigned long long tile = s_tile;
         if (tile >= ntiles) break;
@@ -249,29 +540,65 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
         const long long i0 = (long long)(tile - tile_prefix[lo]) * tile_rows;
         const long long i1 = min(i0 + (long long)tile_rows, rows_end);
         const long long kl = k0 + lane_off;        // slot d walks diagonal kl + d
-        const S4 *__restrict__ rS = Tr::rs(P);
-        const S4 *__restrict__ cS = Tr::cs(P);
+        S4 *rS = Tr::rs(P);
+        S4 *cS = Tr::cs(P);
         Key *rKey = reinterpret_cast<Key *>(P.rKey);
         Key *cKey = reinterpret_cast<Key *>(P.cKey);
 
         T c[D];
-        for (long long r = i0; r < i1; r += RC) {
+        // error bias of the FP32 recurrence: an estimate E of the accumulated
+        // rounding of each covariance since its anchor is kept added to it, so
+        // the fast path compares (statistical) upper bounds of the correlations.
+        // Rounding errors of N steps behave like a random walk: their standard
+        // deviation is about 0.41 eps sqrt(N) |c|, with |c| <= s_i s_j.  E uses
+        // the chunks' RMS norms and update terms (largest RMS since the anchor)
+        // and about five standard deviations:
+        //   E = kBiasSigma eps C sqrt(N + 16),  C = s_R s_C + 2 (df_R dg_C + df_C dg_R).
+        float e_c = 0.0f, e_applied = 0.0f;
+        int e_steps = 0;
+        int chunk = 0;
+        for (long long r = i0; r < i1; r += RC, ++chunk) {
             const int nrows = (int)min((long long)RC, i1 - r);
             const int nrr = (nrows + D - 1) / D * D;
+            const int par = (chunk & 1) * 8;
             __syncthreads();
-            for (int t = threadIdx.x; t < nrr; t += NT) {
-                const long long i = r + t;
-                const S4 v = rS[i];
-                const T thr = (v.w != (T)0 || i >= lR) ? INF : Tr::thr_of(rKey, i);
-                sRow[t] = make4<Tr>(v.x, v.y, v.z, thr);
-            }
-            const long long cb = r + k0;
-            const int ncols = nrr + TD;
-            for (int t = threadIdx.x; t < ncols; t += NT) {
-                const long long j = cb + t;
-                const S4 v = cS[j];
-                const T thr = (v.w != (T)0 || j >= lC) ? INF : Tr::thr_of(cKey, j);
-                sCol[cpos<D>(t)] = make4<Tr>(v.x, v.y, v.z, thr);
+            // stage {df, dg, invn, thr} of the chunk's rows and columns: plain
+            // copies (L2 reads, so thresholds raised by other CTAs are seen),
+            // loads batched ahead of the stores
+            {
+                constexpr int U = 4;
+                float mx[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int t0 = threadIdx.x; t0 < nrr; t0 += NT * U) {
+                    S4 v[U];
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (t0 + k * NT < nrr) v[k] = Tr::ld(rS + r + t0 + k * NT);
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (t0 + k * NT < nrr) {
+                            sRow[t0 + k * NT] = v[k];
+                            if (Tr::kBias) track_max(mx, v[k]);
+                        }
+                }
+                const long long cb = r + k0;
+                const int ncols = nrr + TD;
+                for (int t0 = threadIdx.x; t0 < ncols; t0 += NT * U) {
+                    S4 v[U];
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (t0 + k * NT < ncols) v[k] = Tr::ld(cS + cb + t0 + k * NT);
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (t0 + k * NT < ncols) {
+                            sCol[cpos<D>(t0 + k * NT)] = v[k];
+                            if (Tr::kBias) track_max(mx + 4, v[k]);
+                        }
+                }
+                if (Tr::kBias) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (mx[k] > 0.f) atomicAdd(&s_mx[par + k], mx[k]);
+                }
             }
             __syncthreads();
             if (r == i0 || (anchor_every > 0 && (r - i0) % anchor_every == 0)) {
@@ -279,6 +606,23 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 // r = 0 the update of row 0 adds 0 (df_0 = dg_0 = 0)
                 const long long a = r > 0 ? r - 1 : 0;
                 anchor_covariances<Tr, D>(P, a, a + kl, c);
+                e_c = 0.0f;
+                e_applied = 0.0f;
+                e_steps = 0;
+            }
+            if (Tr::kBias) {
+                const float nr = fmaxf(s_mx[par + 3], 1.0f), nc = fmaxf(s_mx[par + 7], 1.0f);
+                const float sr = sqrtf(s_mx[par] / nr), fr = sqrtf(s_mx[par + 1] / nr),
+                            gr = sqrtf(s_mx[par + 2] / nr), sc = sqrtf(s_mx[par + 4] / nc),
+                            fc = sqrtf(s_mx[par + 5] / nc), gc = sqrtf(s_mx[par + 6] / nc);
+                if (threadIdx.x < 8) s_mx[8 - par + threadIdx.x] = 0.0f;  // the next chunk's set
+                e_c = fmaxf(e_c, sr * sc + 2.0f * (fr * gc + fc * gr));
+                e_steps += nrr;
+                const float e = kBiasSigma * (float)Tr::kEps * e_c * sqrtf((float)(e_steps + 16));
+                const T inc = (T)(e - e_applied);
+                e_applied = e;
+#pragma unroll
+                for (int d = 0; d < D; ++d) c[d] += inc;
             }
             S4 cs[D];
 #pragma unroll
@@ -304,47 +648,17 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     cs[u % D] = sCol[cpos<D>(lane_off + s + u + D)];
                 }
                 if (__any_sync(0xffffffffu, hit)) {
-                    // replay the D rows from c0 with bookkeeping
-                    for (int u = 0; u < D; ++u) {
-                        const S4 rw = sRow[s + u];
-                        const long long i = r + s + u;
-                        T rho[D];
-                        bool prow = false;
+                    // replay the D rows from c0 with bookkeeping (out of line: it is
+                    // rare, and keeping it out of the loop keeps the loop's registers)
+                    CovArr<T, D> cv;
 #pragma unroll
-                        for (int d = 0; d < D; ++d) {
-                            const int q = cpos<D>(lane_off + s + u + d);
-                            const S4 cc = sCol[q];
-                            c0[d] = Tr::fma_(rw.x, cc.y, c0[d]);
-                            c0[d] = Tr::fma_(cc.x, rw.y, c0[d]);
-                            rho[d] = c0[d] * cc.z * rw.z;
-                            prow |= (rho[d] >= rw.w);
-                            if (rho[d] >= cc.w) {
-                                Tr::merge(cKey, i + kl + d, Tr::pack(rho[d], i), hdr);
-                                sCol[q].w = rho[d];
-                            }
-                        }
-                        if (__any_sync(0xffffffffu, prow)) {
-                            Packed best = Tr::pzero();
-#pragma unroll
-                            for (int d = 0; d < D; ++d) {
-                                if (rho[d] >= rw.w) {
-                                    const Packed p = Tr::pack(rho[d], i + kl + d);
-                                    if (Tr::pgt(p, best)) best = p;
-                                }
-                            }
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                const Packed y = Tr::pshfl(best, o);
-                                if (Tr::pgt(y, best)) best = y;
-                            }
-                            if (lane == 0) {
-                                Tr::merge(rKey, i, best, hdr);
-                                const T v = Tr::pval(best);
-                                if (v > sRow[s + u].w) sRow[s + u].w = v;
-                            }
-                        }
-                        __syncwarp();
-                    }
+                    for (int d = 0; d < D; ++d) cv.v[d] = c0[d];
+                    if constexpr (Tr::kBias)
+                        replay_group_f32<D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, cv, r, s, kl,
+                                            lane_off, lane, e_applied);
+                    else
+                        replay_group<Tr, D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, cv, r, s, kl,
+                                            lane_off, lane);
 #pragma unroll
                     for (int d = 0; d < D; ++d) cs[d].w = sCol[cpos<D>(lane_off + s + D + d)].w;
                 }

@@ -122,7 +122,7 @@ __device__ __forceinline__ long long first_diag(int m, double ez, unsigned flags
 __global__ void family_descs_kernel(FamilyParams F)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t ksz = F.fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    const size_t ksz = sizeof(Key128);
     if (F.kind == 0 || F.kind == 2) {          // self-join / pan: one set, problem, output per m
         const int nset = F.kind == 0 ? 1 : F.nm;
         if (k >= nset) return;
@@ -130,13 +130,15 @@ __global__ void family_descs_kernel(FamilyParams F)
         const long long l = F.n - m + 1;
         const long long sb = (long long)k * (F.n + kPad);
         StatSet S;
-        S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.pad = 0;
+        S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.partner = k;
+        S.kmin = first_diag(m, F.ez, F.flags);
         F.sets[k] = S;
         Prob P;
         P.rS32 = P.cS32 = F.s32 ? F.s32 + sb : nullptr;
         P.rS64 = P.cS64 = F.s64 + sb;
         P.rX = P.cX = F.x64;
         P.rMu = P.cMu = F.mu + sb;
+        P.rInv = P.cInv = F.inv + sb;
         P.rKey = P.cKey = F.keys + (size_t)sb * ksz;
         P.lR = P.lC = l;
         P.nC = F.n;
@@ -149,7 +151,8 @@ __global__ void family_descs_kernel(FamilyParams F)
         D.key = P.rKey;
         D.xR = D.xC = F.x64;
         D.muR = D.muC = P.rMu;
-        D.sR = D.sC = P.rS64;
+        D.invR = D.invC = P.rInv;
+        D.flatR = D.flatC = F.flat + sb;
         D.l = l; D.lC = l;
         D.kmin = P.kmin;
         D.pad_to = F.kind == 0 ? l : F.out_stride;
@@ -169,7 +172,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     const long long sbA = 0, sbB = F.na + kPad;
     const double *xa = F.x64, *xb = F.x64 + F.na;
     StatSet S;
-    S.m = m; S.pad = 0;
+    S.m = m; S.partner = 1 - k; S.kmin = -1;
     if (k == 0) { S.x = xa; S.n = F.na; S.l = la; S.sbase = sbA; }
     else { S.x = xb; S.n = F.nb; S.l = lb; S.sbase = sbB; }
     F.sets[k] = S;
@@ -184,6 +187,8 @@ __global__ void family_descs_kernel(FamilyParams F)
     P.cX = rowA ? xb : xa;
     P.rMu = F.mu + sbR;
     P.cMu = F.mu + sbC;
+    P.rInv = F.inv + sbR;
+    P.cInv = F.inv + sbC;
     P.rKey = F.keys + (size_t)sbR * ksz;
     P.cKey = F.keys + (size_t)sbC * ksz;
     P.lR = rowA ? la : lb;
@@ -196,8 +201,8 @@ __global__ void family_descs_kernel(FamilyParams F)
     F.probs[k] = P;
     FinDesc D;
     D.key = P.rKey;
-    D.xR = P.rX; D.muR = P.rMu; D.sR = P.rS64;
-    D.xC = P.cX; D.muC = P.cMu; D.sC = P.cS64;
+    D.xR = P.rX; D.muR = P.rMu; D.invR = P.rInv; D.flatR = F.flat + sbR;
+    D.xC = P.cX; D.muC = P.cMu; D.invC = P.cInv; D.flatC = F.flat + sbC;
     D.l = P.lR; D.lC = P.lC;
     D.kmin = -1;
     D.pad_to = P.lR;
@@ -212,13 +217,14 @@ __global__ void family_descs_kernel(FamilyParams F)
 __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
                                      const int32_t *__restrict__ ms, int B, double ez,
                                      unsigned flags, int fp64, const double *x64, double *mu,
-                                     float4 *s32, D4 *s64, char *keys, double *mp,
+                                     double *inv, float4 *s32, D4 *s64, uint8_t *flat, char *keys,
+                                     double *mp,
                                      int64_t *pi, const int64_t *__restrict__ out_offsets,
                                      StatSet *sets, Prob *probs, FinDesc *fins, Hdr *hdr)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    const size_t ksz = fp64 ? sizeof(Key128) : sizeof(unsigned long long);
+    const size_t ksz = sizeof(Key128);
     const long long o0 = offsets[0];
     const long long off = offsets[b] - o0;
     const long long n = offsets[b + 1] - offsets[b];
@@ -236,13 +242,15 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     }
     const long long sb = off + (long long)b * kPad;
     StatSet S;
-    S.x = x64 + off; S.n = n; S.l = l; S.sbase = sb; S.m = m; S.pad = 0;
+    S.x = x64 + off; S.n = n; S.l = l; S.sbase = sb; S.m = m; S.partner = b;
+    S.kmin = first_diag(m, ez, flags);
     sets[b] = S;
     Prob P;
     P.rS32 = P.cS32 = s32 ? s32 + sb : nullptr;
     P.rS64 = P.cS64 = s64 + sb;
     P.rX = P.cX = x64 + off;
     P.rMu = P.cMu = mu + sb;
+    P.rInv = P.cInv = inv + sb;
     P.rKey = P.cKey = keys + (size_t)sb * ksz;
     P.lR = P.lC = l;
     P.nC = n;
@@ -255,7 +263,8 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     D.key = P.rKey;
     D.xR = D.xC = P.rX;
     D.muR = D.muC = P.rMu;
-    D.sR = D.sC = P.rS64;
+    D.invR = D.invC = P.rInv;
+    D.flatR = D.flatC = flat + sb;
     D.l = l; D.lC = l;
     D.kmin = P.kmin;
     D.pad_to = l;
@@ -277,13 +286,15 @@ cudaError_t launch_family_descs(const FamilyParams &F, cudaStream_t st)
 
 cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int B, double ez,
                                  unsigned flags, int fp64, const double *x64, double *mu,
-                                 float4 *s32, D4 *s64, void *keys, double *mp, int64_t *pi,
+                                 double *inv, float4 *s32, D4 *s64, uint8_t *flat, void *keys,
+                                 double *mp, int64_t *pi,
                                  const int64_t *out_offsets, StatSet *sets, Prob *probs,
                                  FinDesc *fins, Hdr *hdr, cudaStream_t st)
 {
     const int threads = 256;
     batched_descs_kernel<<<(B + threads - 1) / threads, threads, 0, st>>>(
-        offsets, ms, B, ez, flags, fp64, x64, mu, s32, s64, (char *)keys, mp, pi, out_offsets,
+        offsets, ms, B, ez, flags, fp64, x64, mu, inv, s32, s64, flat, (char *)keys, mp, pi,
+        out_offsets,
         sets, probs, fins, hdr);
     return cudaGetLastError();
 }

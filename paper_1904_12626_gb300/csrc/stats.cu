@@ -142,8 +142,10 @@ __global__ void convert_kernel(const T *__restrict__ x, long long n, double *__r
 }
 
 __global__ void stats_sets_kernel(const StatSet *__restrict__ sets, int nsets, long long total,
-                                  double *__restrict__ mu, float4 *__restrict__ s32,
-                                  D4 *__restrict__ s64)
+                                  double *__restrict__ mu, double *__restrict__ inv,
+                                  float4 *__restrict__ s32,
+                                  D4 *__restrict__ s64, uint8_t *__restrict__ flat,
+                                  double *__restrict__ set_acc)
 {
     long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kWindowsPerThread;
     if (g >= total) return;
@@ -169,19 +171,38 @@ __global__ void stats_sets_kernel(const StatSet *__restrict__ sets, int nsets, l
         const long long vend = min(iend, l);
         if (i < vend) {
             const long long base = S.sbase;
+            double logsum = 0.0, cnt = 0.0;
             walk_windows<double>(S.x, S.m, i, vend, [&](long long w, const WindowOut &o) {
+                if (o.invn > 0.0) {                     // norm statistics of the set
+                    logsum -= log(o.invn);
+                    cnt += 1.0;
+                }
                 const long long q = base + w;
                 if (mu) mu[q] = o.mu;
-                const float fl = o.flat ? 1.0f : 0.0f;
-                if (s32) s32[q] = make_float4((float)o.df, (float)o.dg, (float)o.invn, fl);
-                if (s64) s64[q] = make_d4(o.df, o.dg, o.invn, o.flat ? 1.0 : 0.0);
+                if (inv) inv[q] = o.invn;
+                if (flat) flat[q] = o.flat ? 1 : 0;
+                // .w starts as the running threshold of this index: +inf for a flat
+                // window (its answer is closed-form, the tile kernel never updates
+                // it), -inf otherwise (no candidate seen yet)
+                const float t32 = o.flat ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);
+                const double t64 = o.flat ? __longlong_as_double(0x7ff0000000000000ll)
+                                          : __longlong_as_double((long long)0xfff0000000000000ull);
+                if (s32) s32[q] = make_float4((float)o.df, (float)o.dg, (float)o.invn, t32);
+                if (s64) s64[q] = make_d4(o.df, o.dg, o.invn, t64);
             });
+            if (set_acc && cnt > 0.0) {
+                atomicAdd(set_acc + 2 * s, logsum);
+                atomicAdd(set_acc + 2 * s + 1, cnt);
+            }
         }
         for (long long w = (i > l ? i : l); w < iend; ++w) {      // padding entries
             const long long q = S.sbase + w;
             if (mu) mu[q] = 0.0;
-            if (s32) s32[q] = make_float4(0.0f, 0.0f, __int_as_float(0x7fc00000), 0.0f);
-            if (s64) s64[q] = make_d4(0.0, 0.0, __longlong_as_double(0x7ff8000000000000ll), 0.0);
+            if (inv) inv[q] = 0.0;
+            if (flat) flat[q] = 0;
+            if (s32) s32[q] = make_float4(0.0f, 0.0f, __int_as_float(0x7fc00000), __int_as_float(0x7f800000));
+            if (s64) s64[q] = make_d4(0.0, 0.0, __longlong_as_double(0x7ff8000000000000ll),
+                                      __longlong_as_double(0x7ff0000000000000ll));
         }
         g += iend - i;
         if (iend == ext) ++s;
@@ -222,13 +243,15 @@ cudaError_t launch_convert(const void *x, int dtype, long long n, double *x64, H
 }
 
 cudaError_t launch_stats_sets(const StatSet *sets, int nsets, long long total_index, double *mu,
-                              float4 *s32, D4 *s64, cudaStream_t st)
+                              double *inv, float4 *s32, D4 *s64, uint8_t *flat, double *set_acc,
+                              cudaStream_t st)
 {
     if (total_index <= 0 || nsets <= 0) return cudaSuccess;
     const int threads = 128;
     const long long runs = (total_index + kWindowsPerThread - 1) / kWindowsPerThread;
     const long long blocks = (runs + threads - 1) / threads;
-    stats_sets_kernel<<<(unsigned)blocks, threads, 0, st>>>(sets, nsets, total_index, mu, s32, s64);
+    stats_sets_kernel<<<(unsigned)blocks, threads, 0, st>>>(sets, nsets, total_index, mu, inv, s32,
+                                                             s64, flat, set_acc);
     return cudaGetLastError();
 }
 

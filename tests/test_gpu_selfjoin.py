@@ -50,11 +50,12 @@ def test_fp32_without_refine(mp):
     check_rows(x, m, np.arange(len(mp_o)), g_mp, g_pi, mp_o, pi_o, sec_o, 1e-3, excl=32)
 
 
-@pytest.mark.parametrize("prec,variant", [("fp32", 0), ("fp32", 1), ("fp32", 2), ("fp32", 3),
-                                          ("fp64", 0), ("fp64", 1), ("fp64", 2)])
+@pytest.mark.parametrize("prec,variant", [("fp32", v) for v in range(8)] + [("fp64", v) for v in range(3)])
 def test_variants_many_tiles_ragged(mp, prec, variant):
     """Small tiles so the matrix spans many bands and row tiles, with ragged
     tails on both axes; re-anchoring inside tiles."""
+    from paper_1904_12626_gb300 import _lib
+    assert variant < _lib.load().mp_variant_count(1 if prec == "fp32" else 0)
     x = synth.random_walk(3001, seed=3 + variant)
     m = 16
     g_mp, g_pi = _run(mp, x, m, prec=prec, variant=variant, tile_rows=300, anchor_every=128)
@@ -121,6 +122,25 @@ def test_planted_full_size_sampled(mp, prec):
         assert abs(g_pi[p1] - p2) <= 2 and abs(g_pi[p2] - p1) <= 2
     top = int(np.argmax(g_mp))
     assert d - m + 1 <= top <= d + m - 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_near_flat_windows(mp, prec):
+    """Windows that are constant except for a few small steps have norms
+    thousands of times below the rest of the series; their correlations must
+    still be exact.  The step patterns differ between the two stretches, so no
+    two of these windows are exact copies (whose distance 0 would be decided
+    by rounding alone)."""
+    x = synth.random_walk(20000, seed=10)
+    for s0, steps in ((3000, (1.0, -2.0, 3.0, 1.0)), (9000, (-2.0, 1.0, 1.0, -3.0))):
+        x[s0:s0 + 400] = x[s0 - 1]
+        x[s0 + 400:s0 + 404] = x[s0 - 1] + 1e-2 * np.array(steps)
+    m = 128
+    g_mp, g_pi = _run(mp, x, m, prec=prec)
+    rows = np.unique(np.concatenate([np.arange(2800, 3700), np.arange(8800, 9700),
+                                     synth.sample_rows(len(x) - m + 1, 300, seed=11)]))
+    mp_o, pi_o, sec_o = oracle.selfjoin(x, m, rows=rows)
+    check_rows(x, m, rows, g_mp, g_pi, mp_o, pi_o, sec_o, TOL[prec], excl=64)
 
 
 def test_nonfinite_input_is_reported(mp):
