@@ -160,7 +160,7 @@ bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
         if ((call) != cudaSuccess) return MP_ECUDA;   \
     } while (0)
 
-// stats -> keys reset -> [fragile windows marked] -> plan -> persistent join ->
+// stats -> keys reset -> [fragile windows marked] -> keys seeded -> plan -> persistent join ->
 // [fragile pairs exactly] -> finalize
 mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
                    const DeviceInfo *dev, cudaStream_t st)
@@ -172,6 +172,8 @@ mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long l
     MP_CU(cudaMemsetAsync(L.keys, 0, ksz * (size_t)r.S, st));
     MP_CU(launch_fragile_mark(L.sets, r.nsets, max_fin_len, L.set_acc, L.inv, L.flat, L.s32,
                               L.s64, L.frag_list, L.hdr, st));
+    MP_CU(launch_seed(L.sets, r.nsets, max_fin_len, L.mu, L.inv, L.flat, L.s32, L.s64, L.keys,
+                      t.fp64, st));
     MP_CU(launch_plan(L.probs, r.nprob, t.tile_diags, t.tile_rows, L.band_off, L.bands,
                       L.tile_prefix, r.max_bands, L.hdr, st));
     const int bps = t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant];

@@ -187,6 +187,10 @@ cudaError_t launch_fragile_mark(const StatSet *sets, int nsets, long long max_l,
 cudaError_t launch_fragile_pass(const StatSet *sets, const double *mu, const double *inv,
                                 const unsigned long long *frag_list, void *keys, int fp64,
                                 Hdr *hdr, int grid, cudaStream_t st);
+// seed.cu
+cudaError_t launch_seed(const StatSet *sets, int nsets, long long max_l, const double *mu,
+                        const double *inv, const uint8_t *flat, float4 *s32, D4 *s64,
+                        void *keys, int fp64, cudaStream_t st);
 cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, double *mu,
                                 double *invn, double *df, double *dg, uint8_t *flat,
                                 cudaStream_t st);

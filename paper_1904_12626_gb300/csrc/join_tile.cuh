@@ -206,14 +206,27 @@ __device__ __forceinline__ void anchor_covariances(const Prob &P, long long a, l
 // the whole warp (lanes split the window, then a butterfly sum); every lane
 // returns the value.  Column mean omitted for the same reason as in the
 // anchors.
-__device__ __forceinline__ double exact_correlation(const Prob &P, long long i, long long j,
+static __device__ __noinline__ double exact_correlation(const Prob &P, long long i, long long j,
                                                     int lane)
 {
     const double *__restrict__ xr = P.rX + i;
     const double *__restrict__ xc = P.cX + j;
     const double mu = P.rMu[i];
-    double acc = 0.0;
-    for (int t = lane; t < P.m; t += 32) acc = fma(__ldg(xr + t) - mu, __ldg(xc + t), acc);
+    const int m = P.m;
+    double acc0 = 0.0, acc1 = 0.0;
+    int t = lane;
+    for (; t + 96 < m; t += 128) {           // four loads per operand in flight
+        const double a0 = __ldg(xr + t), a1 = __ldg(xr + t + 32), a2 = __ldg(xr + t + 64),
+                     a3 = __ldg(xr + t + 96);
+        const double b0 = __ldg(xc + t), b1 = __ldg(xc + t + 32), b2 = __ldg(xc + t + 64),
+                     b3 = __ldg(xc + t + 96);
+        acc0 = fma(a0 - mu, b0, acc0);
+        acc1 = fma(a1 - mu, b1, acc1);
+        acc0 = fma(a2 - mu, b2, acc0);
+        acc1 = fma(a3 - mu, b3, acc1);
+    }
+    for (; t < m; t += 32) acc0 = fma(__ldg(xr + t) - mu, __ldg(xc + t), acc0);
+    double acc = acc0 + acc1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc * P.rInv[i] * P.cInv[j];
@@ -317,7 +330,7 @@ __device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
 // the warp, one at a time.  For a row key (row_side) the candidate index is
 // a column and the exact pair is (own, idx); for a column key it is a row and
 // the pair is (idx, own).
-__device__ __forceinline__ void warp_merge(const Prob &P, bool pending, Cand c, Key128 *key,
+static __device__ __noinline__ void warp_merge(const Prob &P, bool pending, Cand c, Key128 *key,
                                            bool row_side, long long own, float4 *gthr,
                                            float4 *sthr, int lane, Hdr *hdr)
 {
@@ -331,13 +344,15 @@ __device__ __forceinline__ void warp_merge(const Prob &P, bool pending, Cand c, 
             const int dec = classify(c, cur, kx, kx_idx);
             if (dec == kDiscard) {
                 pending = false;
-                if (kx_idx >= 0 && !key_empty(cur)) {   // keep what was learnt about the key
-                    Cand q = key_cand(cur);
-                    if (q.idx == kx_idx && q.L != q.V) {
-                        q.V = q.L = kx;
-                        if (key_same(cas128(key, cur, cand_key(q)), cur)) raise_thr(gthr, sthr, kx);
-                    }
+                Cand q = key_cand(cur);
+                if (kx_idx >= 0 && q.idx == kx_idx && q.L != q.V) {   // keep what was learnt
+                    q.V = q.L = kx;
+                    if (key_same(cas128(key, cur, cand_key(q)), cur)) raise_thr(gthr, sthr, kx);
                 }
+                // the staged threshold may predate the key's candidate (committed by
+                // another tile): lift it to the key's lower bound, so this tile stops
+                // proposing candidates the key already beats
+                if (sthr && q.L > sthr->w) sthr->w = q.L;
             } else if (dec == kReplace) {
                 if (key_same(cas128(key, cur, cand_key(c)), cur)) {
                     pending = false;
@@ -375,111 +390,258 @@ __device__ __forceinline__ void warp_merge(const Prob &P, bool pending, Cand c, 
     if (pending) set_status(hdr, MP_ETIMEOUT);
 }
 
+// A column candidate of one replayed group, staged in shared memory so the
+// warp's lanes can merge the group's candidates together.
+struct MergeItem {
+    float V, L;
+    int meta;                                   // source lane | slot o << 5 | row u << 10
+    int pad;
+};
+constexpr int kItemsPerWarp = 32;
+
 // FP32-mixed replay of one group of D rows (see cand_f32.cuh for the keys).
-// U = upper bounds from the biased recurrence, the lower bound of a cell is
-// U - 2 ebias invn_i invn_j.  Per row: the top cell by upper bound is the row's
-// candidate; cells whose upper bound reaches its lower bound are verified
-// with it and the best exact one becomes the candidate.  Per column: each cell
-// at or above the column's threshold is a candidate.
+// U = upper bound of a cell's correlation from the biased recurrence; its
+// lower bound is U - W, W = 2 ebias invn_i invn_j.
+//  * Rows: the row's top cell by U is its candidate; cells whose U reaches the
+//    top's lower bound are compared exactly and the best exact one is taken.
+//    Lane u keeps row u's candidate; the D row keys are merged together.
+//  * Columns: a lane meets each of its 2D-1 columns (offset o = u + d) in up
+//    to D cells; every cell at or above the column's threshold competes for
+//    the column's slot.  The slot keeps its top cell by U (lower row on a tie);
+//    if another cell reaches the top's lower bound, the slot's overlapping
+//    cells are compared exactly.  At row u the open slots are u..u+D-1, kept
+//    in a register window that shifts by one per row; a closed slot with a
+//    candidate goes to a short per-lane list.
+// Exact comparisons take a second pass (rare).  The warp's column candidates
+// are then compacted through shared memory and merged one per lane, so a
+// group costs a few global round trips, not one per cell.
 template <int D>
-__device__ __noinline__ void replay_group_f32(const Prob &P, float4 *sRow, float4 *sCol,
-                                              float4 *rS, float4 *cS, Key128 *rKey,
-                                              Key128 *cKey, Hdr *hdr, CovArr<float, D> c0,
-                                              long long r, int s, long long kl, int lane_off,
-                                              int lane, float ebias)
+__device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, float4 *sCol,
+                                                 float4 *rS, float4 *cS, Key128 *rKey,
+                                                 Key128 *cKey, Hdr *hdr, CovArr<float, D> c0,
+                                                 long long r, int s, long long kl, int lane_off,
+                                                 int lane, float ebias, MergeItem *items)
 {
+    constexpr int NS = 2 * D - 1;
+    const long long k0 = kl - lane_off;         // first diagonal of the tile
+    const CovArr<float, D> cstart = c0;
+    // open slots: a?[d] is slot u + d at row u
+    float aU[D], aW[D], a2[D];
+    int au[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        aU[d] = -INFINITY;
+        a2[d] = -INFINITY;
+        aW[d] = 0.0f;
+        au[d] = -1;
+    }
+    // closed slots with a candidate: V, L, meta = o | u << 5 | verify << 10
+    float lV[NS], lL[NS];
+    int lmeta[NS];
+    int ln = 0;
+    unsigned long long rtop = 0ull;             // lane u: row u's top (U, column)
+    float rlt = 0.0f;                           // lane u: the top's lower bound
+    unsigned bandrows = 0u;                     // rows whose top needs exact comparison
+
+    // pass 1: bounds only
+#pragma unroll 1
     for (int u = 0; u < D; ++u) {
         const float4 rw = sRow[s + u];
         const long long i = r + s + u;
-        float U[D], W[D];
-        bool rowc[D], colc[D];
-        bool any = false;
+        float U[D];
+        unsigned long long top = 0ull;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
             c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
             c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
             U[d] = c0.v[d] * cc.z * rw.z;
-            W[d] = 2.0f * ebias * cc.z * rw.z;
-            rowc[d] = U[d] >= rw.w;
-            colc[d] = U[d] >= cc.w;
-            any |= rowc[d] | colc[d];
-        }
-        if (!__any_sync(0xffffffffu, any)) continue;
-
-        // the row's candidate
-        unsigned long long top = 0ull;
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-            if (rowc[d]) {
+            if (U[d] >= cc.w) {
+                if (U[d] > aU[d]) {
+                    a2[d] = aU[d];
+                    aU[d] = U[d];
+                    aW[d] = 2.0f * ebias * cc.z * rw.z;
+                    au[d] = u;
+                } else if (U[d] > a2[d]) {
+                    a2[d] = U[d];
+                }
+            }
+            if (U[d] >= rw.w) {
                 const unsigned long long p = TraitsF32::pack(U[d], i + kl + d);
                 if (p > top) top = p;
             }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
             if (y > top) top = y;
         }
-        Cand rc;
-        rc.V = rc.L = 0.0f;
-        rc.idx = -1;
-        if (top != 0ull) {
+        if (top != 0ull) {                      // warp-uniform
             const long long jt = TraitsF32::pidx(top);
-            const float ut = TraitsF32::pval(top);
-            float wt = 0.0f;
+            const float czt = sCol[cpos<D>((int)(jt - r - k0))].z;
+            const float lt = TraitsF32::pval(top) - 2.0f * ebias * czt * rw.z;
+            bool band = false;
 #pragma unroll
             for (int d = 0; d < D; ++d)
-                if (i + kl + d == jt) wt = W[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
-            const float lt = ut - wt;
-            bool band[D];
-            bool anyband = false;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                band[d] = rowc[d] && (i + kl + d != jt) && U[d] >= lt;
-                anyband |= band[d];
+                band |= (U[d] >= rw.w) && (i + kl + d != jt) && (U[d] >= lt);
+            if (__any_sync(0xffffffffu, band)) bandrows |= 1u << u;
+            if (lane == u) {
+                rtop = top;
+                rlt = lt;
             }
-            if (__any_sync(0xffffffffu, anyband)) {
-                unsigned long long best =
-                    TraitsF32::pack((float)exact_correlation(P, i, jt, lane), jt);
+        }
+        // slot u is closed: list it, shift the window
+        if (au[0] >= 0) {
+            lV[ln] = aU[0];
+            lL[ln] = aU[0] - aW[0];
+            lmeta[ln] = u | (au[0] << 5) | ((a2[0] >= aU[0] - aW[0]) ? 1 << 10 : 0);
+            ++ln;
+        }
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    unsigned mask = __ballot_sync(0xffffffffu, band[d]);
-                    while (mask) {
-                        const int src = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const long long j = __shfl_sync(0xffffffffu, i + kl + d, src);
-                        const unsigned long long p =
-                            TraitsF32::pack((float)exact_correlation(P, i, j, lane), j);
-                        if (p > best) best = p;
-                    }
-                }
-                rc.V = rc.L = TraitsF32::pval(best);
-                rc.idx = TraitsF32::pidx(best);
-            } else {
-                rc.V = ut;
-                rc.L = lt;
-                rc.idx = jt;
-            }
+        for (int d = 0; d + 1 < D; ++d) {
+            aU[d] = aU[d + 1];
+            aW[d] = aW[d + 1];
+            a2[d] = a2[d + 1];
+            au[d] = au[d + 1];
+        }
+        aU[D - 1] = -INFINITY;
+        a2[D - 1] = -INFINITY;
+        aW[D - 1] = 0.0f;
+        au[D - 1] = -1;
+    }
+#pragma unroll
+    for (int d = 0; d + 1 < D; ++d)             // slots D .. 2D-2
+        if (au[d] >= 0) {
+            lV[ln] = aU[d];
+            lL[ln] = aU[d] - aW[d];
+            lmeta[ln] = (D + d) | (au[d] << 5) | ((a2[d] >= aU[d] - aW[d]) ? 1 << 10 : 0);
+            ++ln;
         }
 
-        // merges: each column candidate, then the row candidate (lane 0)
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const long long j = i + kl + d;
-            Cand cc;
-            cc.V = U[d];
-            cc.L = U[d] - W[d];
-            cc.idx = i;
-            warp_merge(P, colc[d], cc, cKey + j, false, j, cS + j,
-                       sCol + cpos<D>(lane_off + s + u + d), lane, hdr);
+    // pass 2 (rare): exact comparisons for overlapping slot cells and row bands
+    bool anyv = false;
+    for (int k = 0; k < ln; ++k) anyv |= (lmeta[k] >> 10) & 1;
+    unsigned long long rex = 0ull;               // lane u: row u's best exact (value, column)
+    if (__any_sync(0xffffffffu, anyv) || bandrows != 0u) {
+        float lo_l[NS];                          // slot o: lower bound of its top, or +inf
+        unsigned long long ex_l[NS];             // slot o: best exact (value, row)
+        for (int o = 0; o < NS; ++o) {
+            lo_l[o] = INFINITY;
+            ex_l[o] = 0ull;
         }
-        warp_merge(P, lane == 0 && rc.idx >= 0, rc, rKey + i, true, i, rS + i, sRow + s + u, lane,
-                   hdr);
+        for (int k = 0; k < ln; ++k)
+            if ((lmeta[k] >> 10) & 1) lo_l[lmeta[k] & 31] = lL[k];
+        c0 = cstart;
+#pragma unroll 1
+        for (int u = 0; u < D; ++u) {
+            const float4 rw = sRow[s + u];
+            const long long i = r + s + u;
+            const bool rb = (bandrows >> u) & 1u;
+            const float ltu = __shfl_sync(0xffffffffu, rlt, u);
+            unsigned long long rbest = 0ull;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
+                c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
+                c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
+                const float Uc = c0.v[d] * cc.z * rw.z;
+                const int o = u + d;
+                const bool need_s = Uc >= lo_l[o];
+                const bool need_r = rb && Uc >= ltu;
+                unsigned mask = __ballot_sync(0xffffffffu, need_s || need_r);
+                while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const long long j = __shfl_sync(0xffffffffu, i + kl + d, src);
+                    const bool ns = __shfl_sync(0xffffffffu, need_s, src);
+                    const bool nr = __shfl_sync(0xffffffffu, need_r, src);
+                    const float e = (float)exact_correlation(P, i, j, lane);
+                    if (ns && lane == src) {
+                        const unsigned long long p = TraitsF32::pack(e, i);
+                        if (p > ex_l[o]) ex_l[o] = p;
+                    }
+                    if (nr) {
+                        const unsigned long long p = TraitsF32::pack(e, j);
+                        if (p > rbest) rbest = p;
+                    }
+                }
+            }
+            if (lane == u && rb) rex = rbest;
+        }
+        for (int k = 0; k < ln; ++k)
+            if ((lmeta[k] >> 10) & 1) {
+                const unsigned long long e = ex_l[lmeta[k] & 31];
+                lV[k] = lL[k] = TraitsF32::pval(e);
+                lmeta[k] = (lmeta[k] & 31) | ((int)(TraitsF32::pidx(e) - (r + s)) << 5);
+            }
+    }
+
+    // column candidates: compact the warp's lists through shared memory and
+    // merge one per lane per step
+    int incl = ln;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - ln;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < total; base += kItemsPerWarp) {
+        for (int k = 0; k < ln; ++k) {
+            const int g = excl + k;
+            if (g >= base && g < base + kItemsPerWarp) {
+                MergeItem it;
+                it.V = lV[k];
+                it.L = lL[k];
+                it.meta = lane | ((lmeta[k] & 31) << 5) | (((lmeta[k] >> 5) & 31) << 10);
+                it.pad = 0;
+                items[g - base] = it;
+            }
+        }
+        __syncwarp();
+        const bool has = base + lane < total;
+        Cand c;
+        c.V = c.L = 0.0f;
+        c.idx = -1;
+        long long j = 0;
+        int q = 0;
+        if (has) {
+            const MergeItem it = items[lane];
+            const int sl = it.meta & 31, o = (it.meta >> 5) & 31, u = it.meta >> 10;
+            // the source lane's first diagonal: lane_off is threadIdx.x * D
+            const int src_off = lane_off + (sl - lane) * D;
+            c.V = it.V;
+            c.L = it.L;
+            c.idx = r + s + u;
+            j = r + s + k0 + src_off + o;
+            q = src_off + s + o;
+        }
+        warp_merge(P, has, c, cKey + j, false, j, cS + j, sCol + cpos<D>(q), lane, hdr);
         __syncwarp();
     }
+
+    // row candidates: lane u merges row u's
+    Cand rc;
+    rc.V = rc.L = 0.0f;
+    rc.idx = -1;
+    if (lane < D && rtop != 0ull) {
+        if ((bandrows >> lane) & 1u) {
+            rc.V = rc.L = TraitsF32::pval(rex);
+            rc.idx = TraitsF32::pidx(rex);
+        } else {
+            rc.V = TraitsF32::pval(rtop);
+            rc.L = rlt;
+            rc.idx = TraitsF32::pidx(rtop);
+        }
+    }
+    const long long ir = r + s + (lane < D ? lane : 0);
+    warp_merge(P, rc.idx >= 0, rc, rKey + ir, true, ir, rS + ir, sRow + s + (lane < D ? lane : 0),
+               lane, hdr);
+    __syncwarp();
 }
+
+// groups the fast path records before their replays run
+constexpr int kQueue = 8;
 
 template <class Tr, int D, int W, int RC>
 struct TileShape {
@@ -487,7 +649,8 @@ struct TileShape {
     static constexpr int TD = NT * D;
     static constexpr int NCOL = RC + TD;
     static constexpr int NCOLP = NCOL + NCOL / D + 1;
-    static constexpr int SMEM = (RC + NCOLP) * (int)sizeof(typename Tr::S4);
+    static constexpr int SMEM_STATS = (RC + NCOLP) * (int)sizeof(typename Tr::S4);
+    static constexpr int SMEM = SMEM_STATS + (Tr::kBias ? W * kItemsPerWarp * (int)sizeof(MergeItem) : 0);
 };
 
 // MINB: minimum resident CTAs per SM the register allocation must allow
@@ -509,6 +672,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     extern __shared__ __align__(32) unsigned char smem_raw[];
     S4 *sRow = reinterpret_cast<S4 *>(smem_raw);
     S4 *sCol = sRow + RC;
+    MergeItem *sItems = reinterpret_cast<MergeItem *>(smem_raw + Sh::SMEM_STATS) +
+                        (threadIdx.x >> 5) * kItemsPerWarp;
     __shared__ unsigned long long s_tile;
     // per-chunk sums of {norm^2, df^2, dg^2, count} over the staged rows and
     // columns (two parity sets of 8): their RMS values size the error bias
@@ -519,6 +684,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     const int nb = hdr->nbands;
     const unsigned long long ntiles = tile_prefix[nb];
     const T INF = Tr::inf();
+    CovArr<T, D> q_c0[kQueue];                 // recorded groups of the current sub-chunk
+    int q_s[kQueue];
 
     for (;;) {
         __syncthreads();
@@ -624,43 +791,51 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
 #pragma unroll
                 for (int d = 0; d < D; ++d) c[d] += inc;
             }
-            S4 cs[D];
+            // the fast path runs over sub-chunks of kQueue groups; a group with a
+            // possible candidate only records its starting covariances, and the
+            // recorded groups are replayed after the sub-chunk, so no call and no
+            // bookkeeping state sits inside the hot loop
+            for (int s0 = 0; s0 < nrr; s0 += kQueue * D) {
+                const int s1 = min(nrr, s0 + kQueue * D);
+                S4 cs[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) cs[d] = sCol[cpos<D>(lane_off + d)];
-
-            for (int s = 0; s < nrr; s += D) {
-                T c0[D];
+                for (int d = 0; d < D; ++d) cs[d] = sCol[cpos<D>(lane_off + s0 + d)];
+                int qn = 0;
+                for (int s = s0; s < s1; s += D) {
+                    T c0[D];
 #pragma unroll
-                for (int d = 0; d < D; ++d) c0[d] = c[d];
-                bool hit = false;
+                    for (int d = 0; d < D; ++d) c0[d] = c[d];
+                    bool hit = false;
 #pragma unroll
-                for (int u = 0; u < D; ++u) {
-                    const S4 rw = sRow[s + u];
+                    for (int u = 0; u < D; ++u) {
+                        const S4 rw = sRow[s + u];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const S4 &cc = cs[(d + u) % D];
-                        c[d] = Tr::fma_(rw.x, cc.y, c[d]);
-                        c[d] = Tr::fma_(cc.x, rw.y, c[d]);
-                        const T rho = c[d] * cc.z * rw.z;
-                        hit |= (rho >= rw.w);
-                        hit |= (rho >= cc.w);
+                        for (int d = 0; d < D; ++d) {
+                            const S4 &cc = cs[(d + u) % D];
+                            c[d] = Tr::fma_(rw.x, cc.y, c[d]);
+                            c[d] = Tr::fma_(cc.x, rw.y, c[d]);
+                            const T rho = c[d] * cc.z * rw.z;
+                            hit |= (rho >= rw.w);
+                            hit |= (rho >= cc.w);
+                        }
+                        cs[u % D] = sCol[cpos<D>(lane_off + s + u + D)];
                     }
-                    cs[u % D] = sCol[cpos<D>(lane_off + s + u + D)];
+                    if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+                        for (int d = 0; d < D; ++d) q_c0[qn].v[d] = c0[d];
+                        q_s[qn] = s;
+                        ++qn;
+                    }
                 }
-                if (__any_sync(0xffffffffu, hit)) {
-                    // replay the D rows from c0 with bookkeeping (out of line: it is
-                    // rare, and keeping it out of the loop keeps the loop's registers)
-                    CovArr<T, D> cv;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) cv.v[d] = c0[d];
+                for (int e = 0; e < qn; ++e) {
+                    // replay a recorded group from its starting covariances, with
+                    // bookkeeping (out of line: it is rare)
                     if constexpr (Tr::kBias)
-                        replay_group_f32<D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, cv, r, s, kl,
-                                            lane_off, lane, e_applied);
+                        replay_group_f32<D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
+                                            q_s[e], kl, lane_off, lane, e_applied, sItems);
                     else
-                        replay_group<Tr, D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, cv, r, s, kl,
-                                            lane_off, lane);
-#pragma unroll
-                    for (int d = 0; d < D; ++d) cs[d].w = sCol[cpos<D>(lane_off + s + D + d)].w;
+                        replay_group<Tr, D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
+                                            q_s[e], kl, lane_off, lane);
                 }
             }
         }
