@@ -23,7 +23,7 @@ struct V {
 // staged chunk), MINB (CTAs per SM the register budget must allow)}
 #define MPGB_F32_VARIANTS(X) \
     X(0, 8, 2, 512, 8) X(1, 8, 4, 512, 4) X(2, 8, 2, 512, 10) X(3, 8, 4, 256, 4) \
-    X(4, 8, 1, 256, 16) X(5, 4, 4, 256, 4) X(6, 16, 2, 256, 2) X(7, 8, 4, 512, 5)
+    X(4, 8, 1, 256, 16) X(5, 8, 2, 256, 12) X(6, 8, 2, 256, 10) X(7, 8, 4, 512, 5)
 
 }  // namespace
 

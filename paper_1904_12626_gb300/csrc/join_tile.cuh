@@ -643,6 +643,67 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
 // groups the fast path records before their replays run
 constexpr int kQueue = 8;
 
+// The hot loop: rows s0 .. s1-1 of the staged chunk (whole groups of D rows)
+// for this thread's D diagonals.  Each cell costs two FMAs (the covariance
+// update), two multiplies (the correlation) and two compares (row and column
+// thresholds).  The column stats walk through a D-entry register ring; the
+// row stats are a shared-memory broadcast.  Returns the number of groups
+// recorded in q_c0 / q_s for replay.
+template <class Tr, int D, int RC>
+static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, int s1,
+                                                 int lane_off, CovArr<typename Tr::T, D> *q_c0,
+                                                 int *q_s)
+{
+    using T = typename Tr::T;
+    using S4 = typename Tr::S4;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    const S4 *sRow = reinterpret_cast<const S4 *>(smem_raw);
+    const S4 *sCol = sRow + RC;
+    T c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = c_io[d];
+    // padded column position of lane_off + s + v (s a multiple of D, v <= D):
+    // q + q / D = (t + s / D) (D + 1) + v with t = lane_off / D, so each group's
+    // column stats sit at constant offsets from one pointer that advances by
+    // D + 1 per group
+    const int t = lane_off / D;
+    const S4 *pc = sCol + (t + s0 / D) * (D + 1);
+    const S4 *pr = sRow + s0;
+    S4 cs[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) cs[d] = pc[d];
+    int qn = 0;
+    for (int s = s0; s < s1; s += D, pc += D + 1, pr += D) {
+        T c0[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) c0[d] = c[d];
+        bool hit = false;
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+            const S4 rw = pr[u];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const S4 &cc = cs[(d + u) % D];
+                c[d] = Tr::fma_(rw.x, cc.y, c[d]);
+                c[d] = Tr::fma_(cc.x, rw.y, c[d]);
+                const T rho = c[d] * cc.z * rw.z;
+                hit |= (rho >= rw.w);
+                hit |= (rho >= cc.w);
+            }
+            cs[u % D] = pc[(D + 1) + u];        // column lane_off + s + u + D
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) q_c0[qn].v[d] = c0[d];
+            q_s[qn] = s;
+            ++qn;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) c_io[d] = c[d];
+    return qn;
+}
+
 template <class Tr, int D, int W, int RC>
 struct TileShape {
     static constexpr int NT = W * 32;
@@ -761,10 +822,14 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                             if (Tr::kBias) track_max(mx + 4, v[k]);
                         }
                 }
-                if (Tr::kBias) {
+                if (Tr::kBias) {                       // warp sums, then one add per warp
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (mx[k] > 0.f) atomicAdd(&s_mx[par + k], mx[k]);
+                    for (int k = 0; k < 8; ++k) {
+                        float v = mx[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0 && v > 0.f) atomicAdd(&s_mx[par + k], v);
+                    }
                 }
             }
             __syncthreads();
@@ -791,42 +856,13 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
 #pragma unroll
                 for (int d = 0; d < D; ++d) c[d] += inc;
             }
-            // the fast path runs over sub-chunks of kQueue groups; a group with a
-            // possible candidate only records its starting covariances, and the
-            // recorded groups are replayed after the sub-chunk, so no call and no
-            // bookkeeping state sits inside the hot loop
+            // the fast path runs over sub-chunks of kQueue groups in a function of
+            // its own (its registers are allocated for the hot loop alone); a group
+            // with a possible candidate only records its starting covariances, and
+            // the recorded groups are replayed after the sub-chunk
             for (int s0 = 0; s0 < nrr; s0 += kQueue * D) {
                 const int s1 = min(nrr, s0 + kQueue * D);
-                S4 cs[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) cs[d] = sCol[cpos<D>(lane_off + s0 + d)];
-                int qn = 0;
-                for (int s = s0; s < s1; s += D) {
-                    T c0[D];
-#pragma unroll
-                    for (int d = 0; d < D; ++d) c0[d] = c[d];
-                    bool hit = false;
-#pragma unroll
-                    for (int u = 0; u < D; ++u) {
-                        const S4 rw = sRow[s + u];
-#pragma unroll
-                        for (int d = 0; d < D; ++d) {
-                            const S4 &cc = cs[(d + u) % D];
-                            c[d] = Tr::fma_(rw.x, cc.y, c[d]);
-                            c[d] = Tr::fma_(cc.x, rw.y, c[d]);
-                            const T rho = c[d] * cc.z * rw.z;
-                            hit |= (rho >= rw.w);
-                            hit |= (rho >= cc.w);
-                        }
-                        cs[u % D] = sCol[cpos<D>(lane_off + s + u + D)];
-                    }
-                    if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll
-                        for (int d = 0; d < D; ++d) q_c0[qn].v[d] = c0[d];
-                        q_s[qn] = s;
-                        ++qn;
-                    }
-                }
+                const int qn = fast_subchunk<Tr, D, RC>(c, s0, s1, lane_off, q_c0, q_s);
                 for (int e = 0; e < qn; ++e) {
                     // replay a recorded group from its starting covariances, with
                     // bookkeeping (out of line: it is rare)
