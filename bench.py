@@ -34,7 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "self-join Gcells/s @n=2^20,m=256: FP32-mixed vs FP64 GPU; % FP32 peak"
 N_DEFAULT, M_DEFAULT, SEED = 1 << 20, 256, 2024
-PROFILE_JSON = os.path.join(ROOT, "profiles", "join_f32_selfjoin_n2p20_m256.json")
+# DRAM traffic of one tile-kernel launch from an ncu capture, with the csrc digest it was taken at
+PROFILE_TXT = os.path.join(ROOT, "profiles", "join_tile_f32_selfjoin_n2p20_m256.txt")
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -218,13 +219,22 @@ def config_block(args, E, cells):
 
 
 def traffic_from_profile():
-    if not os.path.exists(PROFILE_JSON):
+    """dram bytes (read + write) per tile-kernel launch, or None when the kernel
+    sources changed since the capture."""
+    if not os.path.exists(PROFILE_TXT):
         return None
-    with open(PROFILE_JSON) as fh:
-        p = json.load(fh)
-    if p.get("csrc_sha") != csrc_digest():
+    kv = {}
+    with open(PROFILE_TXT) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith((" ", "#", "|")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("csrc_sha") != csrc_digest():
         return None
-    return p.get("dram_bytes_per_launch")
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def run_ours(args, world, rank, local):
@@ -254,8 +264,15 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     api.device_status(ws)
 
-    # convert, descriptors, stats, fragile marking, plan, tile kernel, fragile pass, finalize
-    launches_per_step = 8 if args.prec == "fp32" else 6
+    # convert, descriptors, stats, fragile marking, key seeding, plan, tile kernel,
+    # fragile pass, finalize
+    launches_per_step = 9
+    td, rc = ctypes.c_int32(), ctypes.c_int32()
+    prec_id = 1 if args.prec == "fp32" else 0
+    _lib.check(lib.mp_variant_info(prec_id, cfg.variant, ctypes.byref(td), ctypes.byref(rc)),
+               "mp_variant_info")
+    kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> variant {cfg.variant} "
+                   f"({td.value} diagonals x {rc.value}-row chunks)")
     step_ms, kern_ms = [], []
     kms = ctypes.c_float()
     barrier(world)
@@ -341,7 +358,7 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
                      "frac": achieved / issue_peak, "traffic": traffic_from_profile(),
-                     "kernel": "join_tile_kernel<TraitsF32,8,4,256>", "kernel_ms": kernel_ms,
+                     "kernel": kernel_name, "kernel_ms": kernel_ms,
                      "peak_basis": f"{sms} SMs x 128 lanes x {f_max:.0f} MHz "
                                    f"({'measured max clock' if peaks else 'nominal max clock'})",
                      "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),

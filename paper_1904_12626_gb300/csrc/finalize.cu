@@ -26,12 +26,19 @@ __device__ __forceinline__ double exact_distance(const FinDesc &F, long long i, 
     const double invC = F.invC[j];
     const double muR = F.muR[i], muC = F.muC[j];
     const double *xr = F.xR + i, *xc = F.xC + j;
-    double acc = 0.0;
-    for (int t = 0; t < F.m; ++t) {
-        const double d = (xr[t] - muR) * invR - (xc[t] - muC) * invC;
-        acc = fma(d, d, acc);
+    double a0 = 0.0, a1 = 0.0;                    // two chains: FP64 latency
+    int t = 0;
+    for (; t + 1 < F.m; t += 2) {
+        const double d0 = (xr[t] - muR) * invR - (xc[t] - muC) * invC;
+        const double d1 = (xr[t + 1] - muR) * invR - (xc[t + 1] - muC) * invC;
+        a0 = fma(d0, d0, a0);
+        a1 = fma(d1, d1, a1);
     }
-    double d = sqrt((double)F.m * acc);
+    if (t < F.m) {
+        const double d0 = (xr[t] - muR) * invR - (xc[t] - muC) * invC;
+        a0 = fma(d0, d0, a0);
+    }
+    double d = sqrt((double)F.m * (a0 + a1));
     const double cap = 2.0 * sqrt((double)F.m);
     return d > cap ? cap : d;
 }

@@ -26,9 +26,16 @@ namespace {
 __device__ __forceinline__ double seed_dot(const double *__restrict__ xa, double mua,
                                            const double *__restrict__ xb, int m)
 {
-    double acc = 0.0;
-    for (int t = 0; t < m; ++t) acc = fma(xa[t] - mua, xb[t], acc);
-    return acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;     // four chains: FP64 latency
+    int t = 0;
+    for (; t + 3 < m; t += 4) {
+        a0 = fma(xa[t] - mua, xb[t], a0);
+        a1 = fma(xa[t + 1] - mua, xb[t + 1], a1);
+        a2 = fma(xa[t + 2] - mua, xb[t + 2], a2);
+        a3 = fma(xa[t + 3] - mua, xb[t + 3], a3);
+    }
+    for (; t < m; ++t) a0 = fma(xa[t] - mua, xb[t], a0);
+    return (a0 + a1) + (a2 + a3);
 }
 
 template <bool FP64>
