@@ -140,6 +140,23 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
                       double *mp, int64_t *pi, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Left and right self-join profiles (used by time series chains, Sec. 3.4.4):
+ * for window i, mp_left[i] / pi_left[i] is its nearest neighbour among the
+ * windows j before it (i - j >= E, E the exclusion zone of cfg), and
+ * mp_right[i] / pi_right[i] among the windows after it (j - i >= E).  With
+ * MP_FLAG_EXCL_INCLUSIVE both bounds become > E.  The elementwise minimum of
+ * the two is the self-join profile (ties: the lower index, i.e. the left
+ * side).  A window with no admissible neighbour on a side gets +inf / -1
+ * there; a flat window gets sqrt(2m) and the lowest admissible index of that
+ * side.  All four outputs have l entries (device, overwritten).  ws/ws_bytes:
+ * scratch of at least mp_selfjoin_lr_workspace_bytes(n, cfg) bytes.
+ */
+size_t mp_selfjoin_lr_workspace_bytes(int64_t n, const mp_config *cfg);
+mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                         double *mp_left, int64_t *pi_left, double *mp_right, int64_t *pi_right,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Self-join without a caller workspace (the paper has no counterpart: this
  * is a convenience of the library).  For callers that cannot allocate device
  * memory -- code running inside another framework's CUDA-graph capture, under

@@ -61,6 +61,10 @@ def _bind(lib):
     lib.oracle_selfjoin.restype = ctypes.c_int
     lib.oracle_selfjoin.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int,
                                     _i64, ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
+    lib.oracle_selfjoin_side.restype = ctypes.c_int
+    lib.oracle_selfjoin_side.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int64, _d,
+                                         _i64, _d, ctypes.c_int]
     lib.oracle_abjoin.restype = ctypes.c_int
     lib.oracle_abjoin.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int32,
                                   _i64, ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
@@ -153,6 +157,29 @@ def selfjoin(x, m: int, ez: float = 0.5, rows=None, inclusive: bool = False,
     if rc != 0:
         raise ValueError(f"oracle_selfjoin failed ({rc})")
     return mp, pi, sec
+
+
+def selfjoin_lr(x, m: int, ez: float = 0.5, rows=None, inclusive: bool = False,
+                nthreads: int = 0, lib=None):
+    """Brute-force left and right self-join profiles (candidates before / after
+    each row).  Returns (mp_left, pi_left, sec_left, mp_right, pi_right, sec_right)."""
+    lib = lib or load()
+    x = _f64(x)
+    l = profile_length(len(x), m, lib)
+    rows = np.arange(l, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    excl = exclusion_zone(m, ez, lib)
+    out = []
+    for side in (-1, 1):
+        mp = np.empty(len(rows))
+        pi = np.empty(len(rows), dtype=np.int64)
+        sec = np.empty(len(rows))
+        rc = lib.oracle_selfjoin_side(_p(x, _d), len(x), m, excl, int(inclusive), side,
+                                      _p(rows, _i64), len(rows), _p(mp, _d), _p(pi, _i64),
+                                      _p(sec, _d), nthreads)
+        if rc != 0:
+            raise ValueError(f"oracle_selfjoin_side failed ({rc})")
+        out += [mp, pi, sec]
+    return tuple(out)
 
 
 def abjoin(a, b, m: int, rows=None, nthreads: int = 0, lib=None):

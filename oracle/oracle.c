@@ -191,6 +191,7 @@ typedef struct {
     int64_t lr, lc;
     int32_t m;
     int self;              /* 1: self-join, apply the exclusion zone */
+    int side;              /* self-join: 0 any j, -1 only j < i, +1 only j > i */
     int64_t excl;
     int inclusive;
     const int64_t *rows;
@@ -207,6 +208,7 @@ typedef struct {
 static int admissible(const job_t *J, int64_t i, int64_t j)
 {
     if (!J->self) return 1;
+    if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;
     int64_t d = i > j ? i - j : j - i;
     return J->inclusive ? (d > J->excl) : (d >= J->excl);
 }
@@ -304,6 +306,28 @@ int oracle_selfjoin(const double *x, int64_t n, int32_t m, int64_t excl, int inc
         if (rows[r] < 0 || rows[r] >= l) return -1;
     job_t J = {0};
     J.xr = x; J.xc = x; J.lr = l; J.lc = l; J.m = m; J.self = 1;
+    J.excl = excl; J.inclusive = inclusive;
+    J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
+    return run_join(&J, nthreads);
+}
+
+/*
+ * Left (side = -1) or right (side = +1) self-join profile: as oracle_selfjoin,
+ * with the candidates restricted to the windows before (after) row i.  The
+ * paper's time series chains (Sec. 3.4.4) are built on these two profiles; the
+ * paper gives no formula, so this is the self-join definition above with the
+ * candidate set cut in two.
+ */
+int oracle_selfjoin_side(const double *x, int64_t n, int32_t m, int64_t excl, int inclusive,
+                         int side, const int64_t *rows, int64_t nrows, double *mp, int64_t *pi,
+                         double *second, int nthreads)
+{
+    int64_t l = oracle_profile_length(n, m);
+    if (l <= 0 || m < 2 || (side != -1 && side != 1)) return -1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= l) return -1;
+    job_t J = {0};
+    J.xr = x; J.xc = x; J.lr = l; J.lc = l; J.m = m; J.self = 1; J.side = side;
     J.excl = excl; J.inclusive = inclusive;
     J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
     return run_join(&J, nthreads);

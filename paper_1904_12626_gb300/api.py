@@ -97,6 +97,33 @@ def selfjoin(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *, re
     return mp, pi
 
 
+def selfjoin_lr(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *,
+                refine: bool = True, inclusive: bool = False, tile_rows: int = 0,
+                anchor_every: int = 0, variant: int = 0, ws: torch.Tensor | None = None,
+                stream=None, check_status: bool = False):
+    """Left and right self-join profiles.  Returns (mp_left, pi_left, mp_right, pi_right):
+    the nearest neighbour of each window among the windows before / after it."""
+    x = _prep(x, "x")
+    lib = _lib.load()
+    flags = (0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_EXCL_INCLUSIVE if inclusive else 0)
+    cfg = make_config(m, ez, prec, anchor_every, tile_rows, variant, flags)
+    n = x.numel()
+    l = n - m + 1
+    if m < 4 or l < 1:
+        raise ValueError("need 4 <= m <= n")
+    need = lib.mp_selfjoin_lr_workspace_bytes(n, ctypes.byref(cfg))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, x.device)
+    out = [torch.empty(l, dtype=dt, device=x.device)
+           for dt in (torch.float64, torch.int64, torch.float64, torch.int64)]
+    check(lib.mp_selfjoin_lr(x.data_ptr(), _dtype(x), n, ctypes.byref(cfg),
+                             *(t.data_ptr() for t in out), ws.data_ptr(), ws.numel(),
+                             _stream(stream)), "mp_selfjoin_lr")
+    if check_status:
+        device_status(ws, stream)
+    return tuple(out)
+
+
 def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refine: bool = True,
            both: bool = True, tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
            ws: torch.Tensor | None = None, stream=None, check_status: bool = False):

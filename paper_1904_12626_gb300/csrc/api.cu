@@ -212,6 +212,21 @@ LayoutReq self_req(int64_t n, int32_t m, const TileCfg &t)
     return r;
 }
 
+// left/right self-join: the series' windows twice (right role, left role)
+LayoutReq lr_req(int64_t n, int32_t m, const TileCfg &t)
+{
+    LayoutReq r;
+    const long long l = n - m + 1;
+    r.nx = n;
+    r.S = 2 * (n + kPad);
+    r.nsets = 2;
+    r.nprob = 1;
+    r.nfin = 2;
+    r.max_bands = ceil_div(l > 0 ? l : 0, t.tile_diags) + 1;
+    r.fp64 = t.fp64;
+    return r;
+}
+
 LayoutReq ab_req(int64_t na, int64_t nb, int32_t m, const TileCfg &t)
 {
     LayoutReq r;
@@ -352,6 +367,44 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
     F.kind = 0; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez; F.flags = cfg->flags;
     F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
     F.mp_a = mp; F.pi_a = (long long *)pi; F.out_stride = 0;
+    F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
+    MP_CU(launch_family_descs(F, st));
+    return run_join(L, r, t, n - m + 1, d, st);
+}
+
+size_t mp_selfjoin_lr_workspace_bytes(int64_t n, const mp_config *cfg)
+{
+    TileCfg t;
+    if (resolve(cfg, &t) != MP_OK || n < 1) return 0;
+    return carve(nullptr, lr_req(n, cfg->m, t)).bytes;
+}
+
+mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                         double *mp_left, int64_t *pi_left, double *mp_right, int64_t *pi_right,
+                         void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!x || !mp_left || !pi_left || !mp_right || !pi_right || !ws || !valid_dtype(dtype) ||
+        !aligned256(ws))
+        return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const int32_t m = cfg->m;
+    if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    const LayoutReq r = lr_req(n, m, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(x, dtype, n, L.x64, L.hdr, st));
+    FamilyParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.kind = 3; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez; F.flags = cfg->flags;
+    F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
+    F.mp_a = mp_right; F.pi_a = (long long *)pi_right;
+    F.mp_b = mp_left; F.pi_b = (long long *)pi_left;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
     return run_join(L, r, t, n - m + 1, d, st);

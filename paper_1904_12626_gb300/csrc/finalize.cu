@@ -56,7 +56,10 @@ __device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long
     double mpv = INF;
     long long piv = -1;
     if (F.flatR[i]) {
+        // lowest admissible index (every candidate ties at distance sqrt(2m))
         if (F.kmin < 0) piv = F.lC > 0 ? 0 : -1;
+        else if (F.dir > 0) piv = (i + F.kmin < F.lC) ? i + F.kmin : -1;
+        else if (F.dir < 0) piv = (i >= F.kmin) ? 0 : -1;
         else piv = (i >= F.kmin) ? 0 : ((i + F.kmin < F.lC) ? i + F.kmin : -1);
         if (piv >= 0) mpv = s2m;
     } else {

@@ -159,7 +159,7 @@ fragile_pass_kernel(const StatSet *__restrict__ sets, const double *__restrict__
         Packed best = Tr::pzero();
         for (long long j = tid; j < SY.l; j += blockDim.x) {
             if (SX.kmin >= 0) {                                   // self-join exclusion zone
-                const long long dd = j > f ? j - f : f - j;
+                const long long dd = SX.dir > 0 ? j - f : (SX.dir < 0 ? f - j : (j > f ? j - f : f - j));
                 if (dd < SX.kmin) continue;
             }
             const double muj = ymu[j];

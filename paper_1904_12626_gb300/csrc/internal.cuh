@@ -65,6 +65,9 @@ struct StatSet {
     long long kmin;                       // self-join: first admissible |i-j|; -1: AB pair
     int m;
     int partner;                          // set whose windows are this set's candidates
+    int dir;                              // self-join candidates: 0 both sides, +1 only
+                                          // j > i (right profile), -1 only j < i (left)
+    int pad;
 };
 
 // A window is "fragile" when its centred norm is below kFragileFactor times
@@ -111,12 +114,13 @@ struct FinDesc {
     long long *pi;
     double scale;                         // multiply MP by this (pan normalisation)
     int m;
-    int pad;
+    int dir;                              // as StatSet::dir (flat rows' closed-form PI)
 };
 
 // Parameters of the descriptor kernel of a self-join (kind 0), an AB-join
-// (kind 1) or a pan profile (kind 2); passed by value so that building the
-// descriptors needs no host-to-device copy (capture-safe).
+// (kind 1), a pan profile (kind 2) or a left/right self-join (kind 3); passed
+// by value so that building the descriptors needs no host-to-device copy
+// (capture-safe).
 constexpr int kMaxPan = 256;
 struct FamilyParams {
     int kind;

@@ -132,6 +132,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         StatSet S;
         S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.partner = k;
         S.kmin = first_diag(m, F.ez, F.flags);
+        S.dir = 0; S.pad = 0;
         F.sets[k] = S;
         Prob P;
         P.rS32 = P.cS32 = F.s32 ? F.s32 + sb : nullptr;
@@ -160,7 +161,64 @@ __global__ void family_descs_kernel(FamilyParams F)
         D.pi = F.pi_a + (long long)k * F.out_stride;
         D.scale = (F.flags & MP_FLAG_PAN_NORMALIZE) && F.kind == 2 ? 1.0 / sqrt(2.0 * m) : 1.0;
         D.m = m;
-        D.pad = 0;
+        D.dir = 0;
+        F.fins[k] = D;
+        return;
+    }
+    if (F.kind == 3) {
+        // left/right self-join: the series enters twice, as set 0 (right role:
+        // its keys collect j > i) and set 1 (left role: keys collect j < i);
+        // one problem, rows = set 0, columns = set 1, diagonals E .. l-1, so a
+        // cell (i, i+k) offers j = i+k to i's right key and i to j's left key.
+        if (k >= 2) return;
+        const int m = F.m;
+        const long long l = F.n - m + 1;
+        const long long E = first_diag(m, F.ez, F.flags);
+        const long long sb0 = 0, sb1 = F.n + kPad;
+        const long long sb = k == 0 ? sb0 : sb1;
+        StatSet S;
+        S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.partner = 1 - k;
+        S.kmin = E;
+        S.dir = k == 0 ? 1 : -1; S.pad = 0;
+        F.sets[k] = S;
+        if (k == 0) {
+            Prob P;
+            P.rS32 = F.s32 ? F.s32 + sb0 : nullptr;
+            P.cS32 = F.s32 ? F.s32 + sb1 : nullptr;
+            P.rS64 = F.s64 + sb0;
+            P.cS64 = F.s64 + sb1;
+            P.rX = P.cX = F.x64;
+            P.rMu = F.mu + sb0;
+            P.cMu = F.mu + sb1;
+            P.rInv = F.inv + sb0;
+            P.cInv = F.inv + sb1;
+            P.rKey = F.keys + (size_t)sb0 * ksz;
+            P.cKey = F.keys + (size_t)sb1 * ksz;
+            P.lR = P.lC = l;
+            P.nC = F.n;
+            P.kmin = E;
+            P.kmax = l - 1;
+            P.m = m;
+            P.pad = 0;
+            F.probs[0] = P;
+        }
+        FinDesc D;
+        D.key = F.keys + (size_t)sb * ksz;
+        D.xR = D.xC = F.x64;
+        D.muR = F.mu + sb;
+        D.muC = F.mu + (k == 0 ? sb1 : sb0);
+        D.invR = F.inv + sb;
+        D.invC = F.inv + (k == 0 ? sb1 : sb0);
+        D.flatR = F.flat + sb;
+        D.flatC = F.flat + (k == 0 ? sb1 : sb0);
+        D.l = l; D.lC = l;
+        D.kmin = E;
+        D.pad_to = l;
+        D.mp = k == 0 ? F.mp_a : F.mp_b;
+        D.pi = k == 0 ? F.pi_a : F.pi_b;
+        D.scale = 1.0;
+        D.m = m;
+        D.dir = S.dir;
         F.fins[k] = D;
         return;
     }
@@ -172,7 +230,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     const long long sbA = 0, sbB = F.na + kPad;
     const double *xa = F.x64, *xb = F.x64 + F.na;
     StatSet S;
-    S.m = m; S.partner = 1 - k; S.kmin = -1;
+    S.m = m; S.partner = 1 - k; S.kmin = -1; S.dir = 0; S.pad = 0;
     if (k == 0) { S.x = xa; S.n = F.na; S.l = la; S.sbase = sbA; }
     else { S.x = xb; S.n = F.nb; S.l = lb; S.sbase = sbB; }
     F.sets[k] = S;
@@ -210,7 +268,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     D.pi = rowA ? F.pi_a : F.pi_b;
     D.scale = 1.0;
     D.m = m;
-    D.pad = 0;
+    D.dir = 0;
     F.fins[k] = D;
 }
 
@@ -244,6 +302,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     StatSet S;
     S.x = x64 + off; S.n = n; S.l = l; S.sbase = sb; S.m = m; S.partner = b;
     S.kmin = first_diag(m, ez, flags);
+    S.dir = 0; S.pad = 0;
     sets[b] = S;
     Prob P;
     P.rS32 = P.cS32 = s32 ? s32 + sb : nullptr;
@@ -272,7 +331,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     D.pi = (long long *)pi + out_offsets[b];
     D.scale = 1.0;
     D.m = m;
-    D.pad = 0;
+    D.dir = 0;
     fins[b] = D;
 }
 

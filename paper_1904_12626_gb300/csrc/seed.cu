@@ -11,6 +11,7 @@
 // partner starts the thresholds near their final values:
 //   self-join: partners w + kmin and w - kmin (the nearest admissible
 //              windows; the higher exact correlation, the lower index on a tie);
+//              a left (right) profile takes only w - kmin (w + kmin);
 //   AB-join:   partner min(w, l_partner - 1).
 // The seed is a genuine candidate of the join (exact, admissible), so the
 // answer is unchanged: it only prunes cells that could not win.
@@ -54,8 +55,8 @@ __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__re
         if (flat[q]) continue;                     // closed form, never joined
         long long j1, j2;
         if (S.kmin >= 0) {
-            j1 = w - S.kmin;                       // lower index first: wins ties
-            j2 = w + S.kmin;
+            j1 = S.dir <= 0 ? w - S.kmin : -1;     // lower index first: wins ties
+            j2 = S.dir >= 0 ? w + S.kmin : -1;
             if (j1 < 0) j1 = -1;
             if (j2 >= Y.l) j2 = -1;
         } else {

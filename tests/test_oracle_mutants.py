@@ -32,6 +32,8 @@ MUTANTS = {
                         "grad_x[i + k] += -g[i] * (zi[k] - rho * zj[k]) / (si * d);"),
     "flat_distance": ("if (fi || J->cflat[j]) {\n                d = flatd;",
                       "if (fi || J->cflat[j]) {\n                d = 2.0 * sqrt((double)m);"),
+    "lr_sides_swapped": ("if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;",
+                         "if ((J->side > 0 && j >= i) || (J->side < 0 && j <= i)) return 0;"),
 }
 
 

@@ -50,10 +50,11 @@ def test_paper_printed_sizes():
     assert oracle.exclusion_zone(50, 0.25) == 13
 
 
-def _scipy_profile(x, m, excl=None, inclusive=False, y=None):
+def _scipy_profile(x, m, excl=None, inclusive=False, y=None, side=0):
     """MP/PI by scipy: z-normalise every window (population std), full
     Euclidean distance matrix, mask, row minimum.  Flat windows follow the
-    stated convention (distance sqrt(2m) to everything)."""
+    stated convention (distance sqrt(2m) to everything).  side = -1 / +1
+    keeps only the candidates before / after each row."""
     wa = sliding_window_view(np.asarray(x, np.float64), m)
     wb = wa if y is None else sliding_window_view(np.asarray(y, np.float64), m)
     flat_a = np.ptp(wa, axis=1) == 0
@@ -71,6 +72,10 @@ def _scipy_profile(x, m, excl=None, inclusive=False, y=None):
     if excl is not None:
         ii, jj = np.indices(D.shape)
         bad = np.abs(ii - jj) <= excl if inclusive else np.abs(ii - jj) < excl
+        if side < 0:
+            bad |= jj >= ii
+        elif side > 0:
+            bad |= jj <= ii
         D[bad] = np.inf
     pi = np.argmin(D, axis=1)
     mp = D[np.arange(len(D)), pi]
@@ -164,6 +169,35 @@ def test_selfjoin_against_scipy_bruteforce(n, m, ez, inclusive, seed):
     sep = gap > 1e-9
     np.testing.assert_array_equal(pi[sep], pi_s[sep])
     np.testing.assert_allclose((sec - mp)[sep], gap[sep], atol=1e-9)
+
+
+@pytest.mark.parametrize("n,m,ez,inclusive,seed", [
+    (64, 8, 0.5, False, 11), (120, 8, 0.25, True, 12), (301, 16, 0.5, False, 13)])
+def test_selfjoin_lr_against_scipy_bruteforce(n, m, ez, inclusive, seed):
+    """Left / right profiles (the basis of time series chains, Sec. 3.4.4):
+    the self-join definition with the candidates cut at the row."""
+    x = synth.random_walk(n, seed=seed)
+    if seed == 13:
+        x[40:70] = x[39]                      # flat windows on both sides
+    E = oracle.exclusion_zone(m, ez)
+    ml, pl, sl, mr, pr, sr = oracle.selfjoin_lr(x, m, ez, inclusive=inclusive)
+    for side, mp, pi, sec in ((-1, ml, pl, sl), (1, mr, pr, sr)):
+        mp_s, pi_s, gap = _scipy_profile(x, m, E, inclusive, side=side)
+        np.testing.assert_array_equal(np.isinf(mp), np.isinf(mp_s))
+        fin = np.isfinite(mp_s)
+        np.testing.assert_allclose(mp[fin], mp_s[fin], rtol=0, atol=1e-10)
+        np.testing.assert_array_equal(pi[~fin], -1)
+        sep = fin & (gap > 1e-9)
+        np.testing.assert_array_equal(pi[sep], pi_s[sep])
+    # no left neighbour for the first E rows, no right one for the last E
+    first = E + 1 if inclusive else E
+    assert np.all(np.isinf(ml[:first])) and np.all(np.isfinite(ml[first:]))
+    assert np.all(np.isinf(mr[-first:])) and np.all(np.isfinite(mr[:-first]))
+    # the two sides together are the self-join
+    mp, pi, _ = oracle.selfjoin(x, m, ez, inclusive=inclusive)
+    np.testing.assert_array_equal(np.minimum(ml, mr), mp)
+    take_left = ml <= mr
+    np.testing.assert_array_equal(np.where(take_left, pl, pr), pi)
 
 
 def test_abjoin_against_scipy_bruteforce():
