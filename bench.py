@@ -33,6 +33,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "self-join Gcells/s @n=2^20,m=256: FP32-mixed vs FP64 GPU; % FP32 peak"
+# --join lr: the same workload through the left/right-profile entry point
+METRIC_LR = "left/right self-join Gcells/s @n=2^20,m=256 (FP32-mixed)"
 N_DEFAULT, M_DEFAULT, SEED = 1 << 20, 256, 2024
 # DRAM traffic of one tile-kernel launch from an ncu capture, with the csrc digest it was taken at
 PROFILE_TXT = os.path.join(ROOT, "profiles", "join_tile_f32_selfjoin_n2p20_m256.txt")
@@ -212,8 +214,10 @@ def run_reference(args, world, rank):
 
 
 def config_block(args, E, cells):
-    return {"workload": f"self-join, planted random walk n={args.n} float32, m={args.m}, ez=0.5 "
-                        f"(E={E}), FP32-mixed", "n": args.n, "m": args.m, "cells": cells,
+    kind = "left/right self-join" if getattr(args, "join", "self") == "lr" else "self-join"
+    prec = "FP32-mixed" if args.prec == "fp32" else "FP64"
+    return {"workload": f"{kind}, planted random walk n={args.n} float32, m={args.m}, ez=0.5 "
+                        f"(E={E}), {prec}", "n": args.n, "m": args.m, "cells": cells,
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
@@ -253,11 +257,20 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     import ctypes
     cfg = _lib.make_config(m, 0.5, args.prec)
-    ws = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg)), x.device)
+    lr = args.join == "lr"
+    need = (lib.mp_selfjoin_lr_workspace_bytes if lr else lib.mp_selfjoin_workspace_bytes)(
+        n, ctypes.byref(cfg))
+    ws = api.workspace(need, x.device)
     _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
 
+    def join(xx, prec):
+        """MP and PI (the left/right entry point returns both sides)."""
+        if lr:
+            return api.selfjoin_lr(xx, m, 0.5, prec, ws=ws)
+        return api.selfjoin(xx, m, 0.5, prec, ws=ws)
+
     def step(prec):
-        return api.selfjoin(x, m, 0.5, prec, ws=ws)
+        return join(x, prec)
 
     for _ in range(args.warmup):
         step(args.prec)
@@ -298,7 +311,7 @@ def run_ours(args, world, rank, local):
 
     # all-FP64 kernel on the same input (comparison leg, one warm-up + timed steps)
     fp64 = None
-    if not args.skip_fp64:
+    if not args.skip_fp64 and not lr:
         cfg64 = _lib.make_config(m, 0.5, "fp64")
         ws64 = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg64)), x.device)
         api.selfjoin(x, m, 0.5, "fp64", ws=ws64)
@@ -321,8 +334,8 @@ def run_ours(args, world, rank, local):
 
     # end to end through the public API: pinned host input in, MP/PI back to host
     xh = torch.from_numpy(x_np).pin_memory()
-    mph = torch.empty(l, dtype=torch.float64).pin_memory()
-    pih = torch.empty(l, dtype=torch.int64).pin_memory()
+    host_out = [torch.empty(l, dtype=dt).pin_memory()
+                 for dt in ((torch.float64, torch.int64) * (2 if lr else 1))]
     e2e_ms = []
     for it in range(args.warmup + args.steps):
         flush.fill_(1)
@@ -330,9 +343,9 @@ def run_ours(args, world, rank, local):
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
         xd = xh.to("cuda", non_blocking=True)
-        a, b = api.selfjoin(xd, m, 0.5, args.prec, ws=ws)
-        mph.copy_(a, non_blocking=True)
-        pih.copy_(b, non_blocking=True)
+        res = join(xd, args.prec)
+        for k, (hbuf, dev) in enumerate(zip(host_out, res)):
+            hbuf.copy_(dev, non_blocking=True)
         e.record()
         e.synchronize()
         if it >= args.warmup:
@@ -351,13 +364,14 @@ def run_ours(args, world, rank, local):
     cells_per_s_kernel = cells / (kernel_ms / 1e3)
     achieved = 6 * cells_per_s_kernel / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_LR if lr else METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)",
         "data": "synthetic", "config": config_block(args, E, cells),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
-                     "frac": achieved / issue_peak, "traffic": traffic_from_profile(),
+                     "frac": achieved / issue_peak, "traffic": None if lr else traffic_from_profile(),
                      "kernel": kernel_name, "kernel_ms": kernel_ms,
                      "peak_basis": f"{sms} SMs x 128 lanes x {f_max:.0f} MHz "
                                    f"({'measured max clock' if peaks else 'nominal max clock'})",
@@ -367,7 +381,7 @@ def run_ours(args, world, rank, local):
         "fp64": fp64,
         "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": {"value": e2e_value, "unit": "Gcells/s", "h2d_bytes_per_step": 4 * n,
-                "d2h_bytes_per_step": 16 * l},
+                "d2h_bytes_per_step": 16 * l * (2 if lr else 1)},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
@@ -387,6 +401,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--join", choices=("self", "lr"), default="self")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--m", type=int, default=M_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=1)

@@ -157,6 +157,27 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
                          void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Semantic segmentation from a self-join profile index (FLUSS, Sec. 3.4.3).
+ * pi: l int64 (device; entries < 0 mean "no neighbour"; entries >= l are
+ * skipped and set MP_EINVAL in the workspace status, read it with
+ * mp_get_device_status).  Every window i with pi[i] >= 0 is an arc between
+ * a = min(i, pi[i]) and b = max(i, pi[i]).
+ *   cac[k] (l doubles, device, overwritten) = min(AC[k] / IAC[k], 1), with
+ *   AC[k] = #{i : a_i <= k < b_i} and IAC[k] = 2 k (l - k) / l; cac[k] = 1
+ *   where IAC[k] = 0 and for k < edge or k >= l - edge.
+ *   segments (num_segments int64, device; may be NULL when num_segments = 0):
+ *   the position of the lowest cac (lowest index on ties), then the lowest
+ *   outside |k - s| < seg_excl of every earlier one; -1 once none is left.
+ * The paper (Sec. 3.4.3) shows only the number of segments being chosen; both
+ * margins are left to the caller (the Python binding defaults both to 5m).
+ * ws/ws_bytes: scratch of at least mp_fluss_workspace_bytes(l) bytes.
+ */
+size_t mp_fluss_workspace_bytes(int64_t l);
+mp_status mp_fluss(const int64_t *pi, int64_t l, int64_t edge, int32_t num_segments,
+                   int64_t seg_excl, double *cac, int64_t *segments, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/*
  * Self-join without a caller workspace (the paper has no counterpart: this
  * is a convenience of the library).  For callers that cannot allocate device
  * memory -- code running inside another framework's CUDA-graph capture, under

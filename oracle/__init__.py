@@ -65,6 +65,16 @@ def _bind(lib):
     lib.oracle_selfjoin_side.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                          ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int64, _d,
                                          _i64, _d, ctypes.c_int]
+    lib.oracle_arc_count_at.restype = ctypes.c_int64
+    lib.oracle_arc_count_at.argtypes = [_i64, ctypes.c_int64, ctypes.c_int64]
+    lib.oracle_arc_counts.restype = ctypes.c_int
+    lib.oracle_arc_counts.argtypes = [_i64, ctypes.c_int64, _i64]
+    lib.oracle_arc_counts_fast.restype = ctypes.c_int
+    lib.oracle_arc_counts_fast.argtypes = [_i64, ctypes.c_int64, _i64]
+    lib.oracle_cac.restype = ctypes.c_int
+    lib.oracle_cac.argtypes = [_i64, ctypes.c_int64, ctypes.c_int64, _d]
+    lib.oracle_segments.restype = ctypes.c_int
+    lib.oracle_segments.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _i64]
     lib.oracle_abjoin.restype = ctypes.c_int
     lib.oracle_abjoin.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int32,
                                   _i64, ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
@@ -180,6 +190,41 @@ def selfjoin_lr(x, m: int, ez: float = 0.5, rows=None, inclusive: bool = False,
             raise ValueError(f"oracle_selfjoin_side failed ({rc})")
         out += [mp, pi, sec]
     return tuple(out)
+
+
+def arc_counts(pi, fast: bool = False, lib=None):
+    """Arc count at every position: by the definition (O(l^2)) or by the
+    difference-array form (O(l))."""
+    lib = lib or load()
+    pi = np.ascontiguousarray(pi, dtype=np.int64)
+    ac = np.empty(len(pi), dtype=np.int64)
+    f = lib.oracle_arc_counts_fast if fast else lib.oracle_arc_counts
+    if f(_p(pi, _i64), len(pi), _p(ac, _i64)) != 0:
+        raise ValueError("oracle arc count failed")
+    return ac
+
+
+def arc_count_at(pi, k: int, lib=None) -> int:
+    lib = lib or load()
+    pi = np.ascontiguousarray(pi, dtype=np.int64)
+    return int(lib.oracle_arc_count_at(_p(pi, _i64), len(pi), int(k)))
+
+
+def fluss(pi, m: int, num_segments: int = 2, edge=None, seg_excl=None, fast: bool = True,
+          lib=None):
+    """Corrected arc curve and segment boundaries (margins default to 5 m)."""
+    lib = lib or load()
+    l = len(pi)
+    edge = 5 * m if edge is None else edge
+    seg_excl = 5 * m if seg_excl is None else seg_excl
+    ac = arc_counts(pi, fast=fast, lib=lib)
+    cac = np.empty(l)
+    if lib.oracle_cac(_p(ac, _i64), l, edge, _p(cac, _d)) != 0:
+        raise ValueError("oracle_cac failed")
+    seg = np.empty(num_segments, dtype=np.int64)
+    if lib.oracle_segments(_p(cac, _d), l, num_segments, seg_excl, _p(seg, _i64)) != 0:
+        raise ValueError("oracle_segments failed")
+    return cac, seg
 
 
 def abjoin(a, b, m: int, rows=None, nthreads: int = 0, lib=None):

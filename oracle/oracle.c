@@ -352,6 +352,92 @@ int oracle_abjoin(const double *a, int64_t na, const double *b, int64_t nb, int3
 }
 
 /*
+ * ---- semantic segmentation (Sec. 3.4.3, FLUSS after Gharghabi et al.) ----
+ *
+ * The paper cites the method without formulas; these follow its published
+ * description.  Each window i with a neighbour pi[i] >= 0 is an arc between
+ * a = min(i, pi[i]) and b = max(i, pi[i]); the arc count at position k is the
+ * number of arcs with a <= k < b.  The idealised count for neighbours drawn
+ * uniformly at random is IAC[k] = 2 k (l - k) / l, and the corrected curve is
+ * CAC[k] = min(AC[k] / IAC[k], 1), set to 1 where IAC[k] = 0 and within `edge`
+ * positions of either end.
+ */
+
+/* arc count at one position, straight from the definition: O(l) */
+int64_t oracle_arc_count_at(const int64_t *pi, int64_t l, int64_t k)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < l; ++i) {
+        if (pi[i] < 0 || pi[i] >= l) continue;
+        int64_t a = pi[i] < i ? pi[i] : i, b = pi[i] < i ? i : pi[i];
+        if (a <= k && k < b) ++c;
+    }
+    return c;
+}
+
+/* every position by the definition: O(l^2), for small l */
+int oracle_arc_counts(const int64_t *pi, int64_t l, int64_t *ac)
+{
+    if (l < 1) return -1;
+    for (int64_t k = 0; k < l; ++k) ac[k] = oracle_arc_count_at(pi, l, k);
+    return 0;
+}
+
+/* the same counts in O(l): +1 where an arc starts, -1 where it ends, running sum */
+int oracle_arc_counts_fast(const int64_t *pi, int64_t l, int64_t *ac)
+{
+    if (l < 1) return -1;
+    for (int64_t k = 0; k < l; ++k) ac[k] = 0;
+    for (int64_t i = 0; i < l; ++i) {
+        if (pi[i] < 0 || pi[i] >= l) continue;
+        int64_t a = pi[i] < i ? pi[i] : i, b = pi[i] < i ? i : pi[i];
+        if (a == b) continue;
+        ac[a] += 1;
+        ac[b] -= 1;
+    }
+    for (int64_t k = 1; k < l; ++k) ac[k] += ac[k - 1];
+    return 0;
+}
+
+int oracle_cac(const int64_t *ac, int64_t l, int64_t edge, double *cac)
+{
+    if (l < 1 || edge < 0) return -1;
+    for (int64_t k = 0; k < l; ++k) {
+        double iac = 2.0 * (double)k * (double)(l - k) / (double)l;
+        double c = 1.0;
+        if (k >= edge && k < l - edge && iac > 0.0) {
+            double r = (double)ac[k] / iac;
+            c = r < 1.0 ? r : 1.0;
+        }
+        cac[k] = c;
+    }
+    return 0;
+}
+
+/* boundaries: the lowest cac (lowest index on ties), then the lowest outside
+   |k - s| < seg_excl of every earlier pick; -1 once nothing is left */
+int oracle_segments(const double *cac, int64_t l, int32_t num_segments, int64_t seg_excl,
+                    int64_t *segments)
+{
+    if (l < 1 || num_segments < 0 || seg_excl < 0) return -1;
+    for (int32_t s = 0; s < num_segments; ++s) {
+        int64_t best = -1;
+        for (int64_t k = 0; k < l; ++k) {
+            int masked = 0;
+            for (int32_t t = 0; t < s; ++t) {
+                if (segments[t] < 0) continue;
+                int64_t d = k > segments[t] ? k - segments[t] : segments[t] - k;
+                if (d < seg_excl || d == 0) masked = 1;
+            }
+            if (masked) continue;
+            if (best < 0 || cac[k] < cac[best]) best = k;
+        }
+        segments[s] = best;
+    }
+    return 0;
+}
+
+/*
  * Gradient of L = sum_i g_i * MP_i with respect to x, holding each argmin
  * pair (i, pi[i]) fixed.  With zi, zj the z-normalised windows, rho their
  * correlation (1/m) sum zi zj, d = |zi - zj| and sigma the population

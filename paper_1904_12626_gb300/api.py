@@ -124,6 +124,33 @@ def selfjoin_lr(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *,
     return tuple(out)
 
 
+def fluss(pi: torch.Tensor, m: int, num_segments: int = 2, *, edge: int | None = None,
+          seg_excl: int | None = None, ws: torch.Tensor | None = None, stream=None,
+          check_status: bool = False):
+    """Semantic segmentation (FLUSS) from a self-join profile index.
+    Returns (cac float64 [l], segments int64 [num_segments], -1 when none is left).
+    edge and seg_excl default to 5 m."""
+    if pi.dtype != torch.int64 or not pi.is_cuda:
+        raise TypeError("pi must be an int64 CUDA tensor")
+    pi = pi.contiguous()
+    lib = _lib.load()
+    l = pi.numel()
+    edge = 5 * m if edge is None else edge
+    seg_excl = 5 * m if seg_excl is None else seg_excl
+    need = lib.mp_fluss_workspace_bytes(l)
+    if need == 0:
+        raise ValueError("bad profile length")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, pi.device)
+    cac = torch.empty(l, dtype=torch.float64, device=pi.device)
+    seg = torch.empty(max(num_segments, 1), dtype=torch.int64, device=pi.device)
+    check(lib.mp_fluss(pi.data_ptr(), l, edge, num_segments, seg_excl, cac.data_ptr(),
+                       seg.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "mp_fluss")
+    if check_status:
+        device_status(ws, stream)
+    return cac, seg[:num_segments]
+
+
 def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refine: bool = True,
            both: bool = True, tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
            ws: torch.Tensor | None = None, stream=None, check_status: bool = False):

@@ -372,6 +372,28 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
     return run_join(L, r, t, n - m + 1, d, st);
 }
 
+size_t mp_fluss_workspace_bytes(int64_t l)
+{
+    if (l < 1 || l > kMaxN) return 0;
+    return fluss_workspace_bytes(l);
+}
+
+mp_status mp_fluss(const int64_t *pi, int64_t l, int64_t edge, int32_t num_segments,
+                   int64_t seg_excl, double *cac, int64_t *segments, void *ws, size_t ws_bytes,
+                   void *stream)
+{
+    if (!pi || !cac || !ws || l < 1 || l > kMaxN || edge < 0 || seg_excl < 0 ||
+        num_segments < 0 || (num_segments > 0 && !segments) || !aligned256(ws))
+        return MP_EINVAL;
+    if (ws_bytes < fluss_workspace_bytes(l)) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    const mp_status s = current_device(&d);
+    if (s != MP_OK) return s;
+    MP_CU(launch_fluss(pi, l, edge, num_segments, seg_excl, cac, segments, ws,
+                       (cudaStream_t)stream));
+    return MP_OK;
+}
+
 size_t mp_selfjoin_lr_workspace_bytes(int64_t n, const mp_config *cfg)
 {
     TileCfg t;

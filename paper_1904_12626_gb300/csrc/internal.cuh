@@ -191,6 +191,12 @@ cudaError_t launch_fragile_mark(const StatSet *sets, int nsets, long long max_l,
 cudaError_t launch_fragile_pass(const StatSet *sets, const double *mu, const double *inv,
                                 const unsigned long long *frag_list, void *keys, int fp64,
                                 Hdr *hdr, int grid, cudaStream_t st);
+// fluss.cu
+size_t fluss_workspace_bytes(long long l);
+cudaError_t launch_fluss(const int64_t *pi, long long l, long long edge, int num_segments,
+                         long long seg_excl, double *cac, int64_t *segments, void *ws,
+                         cudaStream_t st);
+
 // seed.cu
 cudaError_t launch_seed(const StatSet *sets, int nsets, long long max_l, const double *mu,
                         const double *inv, const uint8_t *flat, float4 *s32, D4 *s64,

@@ -32,6 +32,9 @@ MUTANTS = {
                         "grad_x[i + k] += -g[i] * (zi[k] - rho * zj[k]) / (si * d);"),
     "flat_distance": ("if (fi || J->cflat[j]) {\n                d = flatd;",
                       "if (fi || J->cflat[j]) {\n                d = 2.0 * sqrt((double)m);"),
+    "arc_end_inclusive": ("if (a <= k && k < b) ++c;", "if (a <= k && k <= b) ++c;"),
+    "iac_scale": ("double iac = 2.0 * (double)k * (double)(l - k) / (double)l;",
+                  "double iac = 1.0 * (double)k * (double)(l - k) / (double)l;"),
     "lr_sides_swapped": ("if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;",
                          "if ((J->side > 0 && j >= i) || (J->side < 0 && j <= i)) return 0;"),
 }
@@ -49,6 +52,7 @@ def test_pins_catch_mutant(name, tmp_path):
                            "-pthread", str(mut_c), "-o", str(so), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(HERE, "test_oracle_pins.py")],
+                        os.path.join(HERE, "test_oracle_pins.py"),
+                        os.path.join(HERE, "test_oracle_fluss.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
