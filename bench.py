@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 METRIC = "self-join Gcells/s @n=2^20,m=256: FP32-mixed vs FP64 GPU; % FP32 peak"
 # --join lr: the same workload through the left/right-profile entry point
 METRIC_LR = "left/right self-join Gcells/s @n=2^20,m=256 (FP32-mixed)"
+METRIC_ANY = "anytime self-join, 5% run then resume to 100%, Gcells/s @n=2^20,m=256 (FP32-mixed)"
 N_DEFAULT, M_DEFAULT, SEED = 1 << 20, 256, 2024
 # DRAM traffic of one tile-kernel launch from an ncu capture, with the csrc digest it was taken at
 PROFILE_TXT = os.path.join(ROOT, "profiles", "join_tile_f32_selfjoin_n2p20_m256.txt")
@@ -214,7 +215,8 @@ def run_reference(args, world, rank):
 
 
 def config_block(args, E, cells):
-    kind = "left/right self-join" if getattr(args, "join", "self") == "lr" else "self-join"
+    kind = {"lr": "left/right self-join", "anytime": "anytime self-join (5% run, resume to 100%)"
+            }.get(getattr(args, "join", "self"), "self-join")
     prec = "FP32-mixed" if args.prec == "fp32" else "FP64"
     return {"workload": f"{kind}, planted random walk n={args.n} float32, m={args.m}, ez=0.5 "
                         f"(E={E}), {prec}", "n": args.n, "m": args.m, "cells": cells,
@@ -258,6 +260,7 @@ def run_ours(args, world, rank, local):
     import ctypes
     cfg = _lib.make_config(m, 0.5, args.prec)
     lr = args.join == "lr"
+    anytime = args.join == "anytime"
     need = (lib.mp_selfjoin_lr_workspace_bytes if lr else lib.mp_selfjoin_workspace_bytes)(
         n, ctypes.byref(cfg))
     ws = api.workspace(need, x.device)
@@ -267,6 +270,10 @@ def run_ours(args, world, rank, local):
         """MP and PI (the left/right entry point returns both sides)."""
         if lr:
             return api.selfjoin_lr(xx, m, 0.5, prec, ws=ws)
+        if anytime:                 # begin, a 5% run, then resume to the full profile
+            run = api.Anytime(xx, m, seed=1, prec=prec, ws=ws)
+            run.run(0.05)
+            return run.run(1.0)
         return api.selfjoin(xx, m, 0.5, prec, ws=ws)
 
     def step(prec):
@@ -279,7 +286,7 @@ def run_ours(args, world, rank, local):
 
     # convert, descriptors, stats, fragile marking, key seeding, plan, tile kernel,
     # fragile pass, finalize
-    launches_per_step = 9
+    launches_per_step = 17 if anytime else 9      # anytime: begin (7) + two runs (5 each)
     td, rc = ctypes.c_int32(), ctypes.c_int32()
     prec_id = 1 if args.prec == "fp32" else 0
     _lib.check(lib.mp_variant_info(prec_id, cfg.variant, ctypes.byref(td), ctypes.byref(rc)),
@@ -307,11 +314,13 @@ def run_ours(args, world, rank, local):
     api.device_status(ws)
     total_ms = max_over_ranks(sum(step_ms), world)
     kernel_ms = max_over_ranks(statistics.mean(kern_ms), world)
+    if anytime:                # the tile kernel runs twice per step: judge the whole step
+        kernel_ms = total_ms / args.steps
     value = world * cells * args.steps / (total_ms / 1e3) / 1e9
 
     # all-FP64 kernel on the same input (comparison leg, one warm-up + timed steps)
     fp64 = None
-    if not args.skip_fp64 and not lr:
+    if not args.skip_fp64 and not lr and not anytime:
         cfg64 = _lib.make_config(m, 0.5, "fp64")
         ws64 = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg64)), x.device)
         api.selfjoin(x, m, 0.5, "fp64", ws=ws64)
@@ -364,7 +373,7 @@ def run_ours(args, world, rank, local):
     cells_per_s_kernel = cells / (kernel_ms / 1e3)
     achieved = 6 * cells_per_s_kernel / 1e12
     line = {
-        "metric": METRIC_LR if lr else METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world,
+        "metric": METRIC_LR if lr else (METRIC_ANY if anytime else METRIC), "value": value, "unit": "Gcells/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)",
@@ -394,6 +403,91 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_fluss(args, world, rank, local):
+    """--join fluss: segmentation of the benchmark input's profile index (the
+    self-join runs once, untimed); each step is one mp_fluss call with two
+    boundaries, L2 flushed in between."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, build
+    build.build()
+    api.init()
+    lib = _lib.load()
+    x_np, _ = workload(args.n, args.m)
+    m = args.m
+    l = args.n - m + 1
+    _, pi = api.selfjoin(torch.from_numpy(x_np).cuda(), m, 0.5, args.prec)
+    ws = api.workspace(lib.mp_fluss_workspace_bytes(l), pi.device)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        api.fluss(pi, m, 2, ws=ws)
+    api.device_status(ws)
+    times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            api.fluss(pi, m, 2, ws=ws)
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+    barrier(world)
+    total_ms = max_over_ranks(sum(times), world)
+    value = world * l * args.steps / (total_ms / 1e3) / 1e6
+    # e2e: the profile index from pinned host memory, CAC and boundaries back
+    pih = pi.cpu().pin_memory()
+    cach = torch.empty(l, dtype=torch.float64).pin_memory()
+    segh = torch.empty(2, dtype=torch.int64).pin_memory()
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        pd = pih.to("cuda", non_blocking=True)
+        c, g = api.fluss(pd, m, 2, ws=ws)
+        cach.copy_(c, non_blocking=True)
+        segh.copy_(g, non_blocking=True)
+        e.record()
+        e.synchronize()
+        if it >= args.warmup:
+            e2e.append(s.elapsed_time(e))
+    e2e_total = max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return
+    ms = total_ms / args.steps
+    # algorithmic bytes per position: PI read 8, marks zeroed 4, two mark
+    # atomics 8, marks read by both scan passes 8, CAC written 8, the
+    # boundary search copies the curve (8 + 8) and reads it per boundary (2 x 8)
+    bpp = 8 + 4 + 8 + 8 + 8 + 16 + 16
+    achieved = bpp * l / (ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    line = {
+        "metric": "FLUSS positions/s @l=2^20 (corrected arc curve + 2 boundaries)",
+        "value": value, "unit": "Mpositions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 counts, f64 curve", "data": "synthetic",
+        "config": {"workload": f"FLUSS on the profile index of the planted random walk "
+                               f"n={args.n}, m={m}", "l": l,
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_basis": "measured copy bandwidth" if peaks else "fallback 6.8 TB/s"},
+        "e2e": {"value": world * l * args.steps / (e2e_total / 1e3) / 1e6, "unit": "Mpositions/s",
+                "h2d_bytes_per_step": 8 * l, "d2h_bytes_per_step": 8 * l + 16},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,7 +495,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
-    ap.add_argument("--join", choices=("self", "lr"), default="self")
+    ap.add_argument("--join", choices=("self", "lr", "anytime", "fluss"), default="self")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--m", type=int, default=M_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -418,7 +512,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
-        run_ours(args, world, rank, local)
+        (run_fluss if args.join == "fluss" else run_ours)(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

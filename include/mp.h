@@ -157,6 +157,32 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
                          void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Anytime self-join (SCRIMP's random diagonal order, Sec. 3.3.3, and the
+ * partial runs the paper's s_size argument controls, Sec. 3.2): the bands of
+ * tile_diags consecutive diagonals (mp_variant_info) are put in a random
+ * order and processed a prefix at a time, so a partial run returns a profile
+ * that is exact over the diagonals done so far (plus the diagonal E every
+ * key is seeded from; pairs of ill-conditioned windows are always done in
+ * full) and converges to the self-join.
+ *   mp_anytime_begin: statistics, seeding, plan and the band order.  The
+ *     order is a Fisher-Yates shuffle of 0..nb-1 driven by splitmix64 from
+ *     `seed`: for i = nb-1 down to 1, swap slots i and r % (i+1), r the next
+ *     splitmix64 output.
+ *   mp_anytime_run: processes the bands up to slot ceil(fraction * nb)
+ *     (fraction in [0, 1], cumulative; a smaller value than before processes
+ *     nothing new) and writes the best-so-far mp / pi (l entries, device).
+ *     fraction = 1 gives the mp_selfjoin result.
+ * Both calls take the same n and cfg and the same workspace of at least
+ * mp_anytime_workspace_bytes(n, cfg) bytes, which holds the state between
+ * runs; runs on one workspace must be serialised.
+ */
+size_t mp_anytime_workspace_bytes(int64_t n, const mp_config *cfg);
+mp_status mp_anytime_begin(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                           uint64_t seed, void *ws, size_t ws_bytes, void *stream);
+mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, double *mp,
+                         int64_t *pi, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Semantic segmentation from a self-join profile index (FLUSS, Sec. 3.4.3).
  * pi: l int64 (device; entries < 0 mean "no neighbour"; entries >= l are
  * skipped and set MP_EINVAL in the workspace status, read it with

@@ -75,6 +75,10 @@ def _bind(lib):
     lib.oracle_cac.argtypes = [_i64, ctypes.c_int64, ctypes.c_int64, _d]
     lib.oracle_segments.restype = ctypes.c_int
     lib.oracle_segments.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _i64]
+    lib.oracle_selfjoin_diags.restype = ctypes.c_int
+    lib.oracle_selfjoin_diags.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_int, _u8, _i64, ctypes.c_int64, _d, _i64, _d,
+                                          ctypes.c_int]
     lib.oracle_abjoin.restype = ctypes.c_int
     lib.oracle_abjoin.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int32,
                                   _i64, ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
@@ -225,6 +229,29 @@ def fluss(pi, m: int, num_segments: int = 2, edge=None, seg_excl=None, fast: boo
     if lib.oracle_segments(_p(cac, _d), l, num_segments, seg_excl, _p(seg, _i64)) != 0:
         raise ValueError("oracle_segments failed")
     return cac, seg
+
+
+def selfjoin_diags(x, m: int, diag_ok, ez: float = 0.5, rows=None, inclusive: bool = False,
+                   nthreads: int = 0, lib=None):
+    """Brute-force self-join over the diagonals |i - j| with diag_ok set (an
+    anytime run's best-so-far).  Returns (mp, pi, second)."""
+    lib = lib or load()
+    x = _f64(x)
+    l = profile_length(len(x), m, lib)
+    ok = np.ascontiguousarray(diag_ok, dtype=np.uint8)
+    if len(ok) != l:
+        raise ValueError("diag_ok needs l entries")
+    rows = np.arange(l, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    excl = exclusion_zone(m, ez, lib)
+    mp = np.empty(len(rows))
+    pi = np.empty(len(rows), dtype=np.int64)
+    sec = np.empty(len(rows))
+    rc = lib.oracle_selfjoin_diags(_p(x, _d), len(x), m, excl, int(inclusive), _p(ok, _u8),
+                                   _p(rows, _i64), len(rows), _p(mp, _d), _p(pi, _i64),
+                                   _p(sec, _d), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle_selfjoin_diags failed ({rc})")
+    return mp, pi, sec
 
 
 def abjoin(a, b, m: int, rows=None, nthreads: int = 0, lib=None):

@@ -192,6 +192,7 @@ typedef struct {
     int32_t m;
     int self;              /* 1: self-join, apply the exclusion zone */
     int side;              /* self-join: 0 any j, -1 only j < i, +1 only j > i */
+    const uint8_t *diag_ok; /* self-join: nullable; j allowed only if diag_ok[|i - j|] */
     int64_t excl;
     int inclusive;
     const int64_t *rows;
@@ -210,6 +211,7 @@ static int admissible(const job_t *J, int64_t i, int64_t j)
     if (!J->self) return 1;
     if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;
     int64_t d = i > j ? i - j : j - i;
+    if (J->diag_ok && !J->diag_ok[d]) return 0;
     return J->inclusive ? (d > J->excl) : (d >= J->excl);
 }
 
@@ -328,6 +330,28 @@ int oracle_selfjoin_side(const double *x, int64_t n, int32_t m, int64_t excl, in
         if (rows[r] < 0 || rows[r] >= l) return -1;
     job_t J = {0};
     J.xr = x; J.xc = x; J.lr = l; J.lc = l; J.m = m; J.self = 1; J.side = side;
+    J.excl = excl; J.inclusive = inclusive;
+    J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
+    return run_join(&J, nthreads);
+}
+
+/*
+ * Self-join restricted to a set of diagonals: j is a candidate of row i only
+ * if diag_ok[|i - j|] (l entries) besides the exclusion zone.  This is what an
+ * anytime run (Sec. 3.3.1, 3.3.3: the best-so-far profile over the distance
+ * profiles / diagonals computed so far) has seen after a given set of
+ * diagonals.
+ */
+int oracle_selfjoin_diags(const double *x, int64_t n, int32_t m, int64_t excl, int inclusive,
+                          const uint8_t *diag_ok, const int64_t *rows, int64_t nrows, double *mp,
+                          int64_t *pi, double *second, int nthreads)
+{
+    int64_t l = oracle_profile_length(n, m);
+    if (l <= 0 || m < 2 || !diag_ok) return -1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= l) return -1;
+    job_t J = {0};
+    J.xr = x; J.xc = x; J.lr = l; J.lc = l; J.m = m; J.self = 1; J.diag_ok = diag_ok;
     J.excl = excl; J.inclusive = inclusive;
     J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
     return run_join(&J, nthreads);

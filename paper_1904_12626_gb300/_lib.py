@@ -59,6 +59,9 @@ SIGNATURES = {
     "mp_selfjoin": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, _vp, _vp, _vp, _sz, _vp]),
     "mp_selfjoin_lr_workspace_bytes": (_sz, [_i64, _cfgp]),
     "mp_fluss_workspace_bytes": (_sz, [_i64]),
+    "mp_anytime_workspace_bytes": (_sz, [_i64, _cfgp]),
+    "mp_anytime_begin": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, ctypes.c_uint64, _vp, _sz, _vp]),
+    "mp_anytime_run": (ctypes.c_int, [_i64, _cfgp, _dbl, _vp, _vp, _vp, _sz, _vp]),
     "mp_fluss": (ctypes.c_int, [_vp, _i64, _i64, _i32, _i64, _vp, _vp, _vp, _sz, _vp]),
     "mp_selfjoin_lr": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mp_selfjoin_noalloc": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, _vp, _vp, _vp]),

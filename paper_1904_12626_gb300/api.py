@@ -124,6 +124,39 @@ def selfjoin_lr(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *,
     return tuple(out)
 
 
+class Anytime:
+    """Anytime self-join: bands of diagonals in a seeded random order, run a
+    cumulative fraction at a time.  `run(f)` returns the best-so-far (mp, pi)."""
+
+    def __init__(self, x: torch.Tensor, m: int, seed: int = 0, ez: float = 0.5,
+                 prec: str = "fp32", *, variant: int = 0, tile_rows: int = 0, stream=None,
+                 ws: torch.Tensor | None = None):
+        self.x = _prep(x, "x")
+        self.lib = _lib.load()
+        self.cfg = make_config(m, ez, prec, 0, tile_rows, variant, 0)
+        self.n = self.x.numel()
+        self.l = self.n - m + 1
+        if m < 4 or self.l < 1:
+            raise ValueError("need 4 <= m <= n")
+        self.stream = stream
+        need = self.lib.mp_anytime_workspace_bytes(self.n, ctypes.byref(self.cfg))
+        self.ws = ws if ws is not None and ws.numel() >= need else workspace(need, self.x.device)
+        check(self.lib.mp_anytime_begin(self.x.data_ptr(), _dtype(self.x), self.n,
+                                        ctypes.byref(self.cfg), int(seed) & (2**64 - 1),
+                                        self.ws.data_ptr(), self.ws.numel(), _stream(stream)),
+              "mp_anytime_begin")
+
+    def run(self, fraction: float, check_status: bool = False):
+        mp = torch.empty(self.l, dtype=torch.float64, device=self.x.device)
+        pi = torch.empty(self.l, dtype=torch.int64, device=self.x.device)
+        check(self.lib.mp_anytime_run(self.n, ctypes.byref(self.cfg), float(fraction),
+                                      mp.data_ptr(), pi.data_ptr(), self.ws.data_ptr(),
+                                      self.ws.numel(), _stream(self.stream)), "mp_anytime_run")
+        if check_status:
+            device_status(self.ws, self.stream)
+        return mp, pi
+
+
 def fluss(pi: torch.Tensor, m: int, num_segments: int = 2, *, edge: int | None = None,
           seg_excl: int | None = None, ws: torch.Tensor | None = None, stream=None,
           check_status: bool = False):

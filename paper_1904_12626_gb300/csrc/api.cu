@@ -120,6 +120,7 @@ struct Layout {
     long long *band_off;
     Band *bands;
     unsigned long long *tile_prefix;
+    long long *scratch;      // band reordering (anytime): 32 bytes per band
     size_t bytes;
 };
 
@@ -149,6 +150,7 @@ Layout carve(void *base, const LayoutReq &r)
     L.band_off = (long long *)take(sizeof(long long) * (size_t)(r.nprob + 1));
     L.bands = (Band *)take(sizeof(Band) * (size_t)(r.max_bands > 0 ? r.max_bands : 1));
     L.tile_prefix = (unsigned long long *)take(sizeof(unsigned long long) * (size_t)(r.max_bands + 1));
+    L.scratch = (long long *)take(32 * (size_t)(r.max_bands > 0 ? r.max_bands : 1));
     L.bytes = (off + 255) & ~(size_t)255;
     return L;
 }
@@ -160,10 +162,9 @@ bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
         if ((call) != cudaSuccess) return MP_ECUDA;   \
     } while (0)
 
-// stats -> keys reset -> [fragile windows marked] -> keys seeded -> plan -> persistent join ->
-// [fragile pairs exactly] -> finalize
-mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
-                   const DeviceInfo *dev, cudaStream_t st)
+// stats -> keys reset -> [fragile windows marked] -> keys seeded -> plan
+mp_status prepare_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
+                       cudaStream_t st)
 {
     MP_CU(cudaMemsetAsync(L.set_acc, 0, sizeof(double) * 2 * (size_t)r.nsets, st));
     MP_CU(launch_stats_sets(L.sets, r.nsets, r.S, L.mu, L.inv, L.s32, L.s64, L.flat, L.set_acc,
@@ -176,6 +177,13 @@ mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long l
                       t.fp64, st));
     MP_CU(launch_plan(L.probs, r.nprob, t.tile_diags, t.tile_rows, L.band_off, L.bands,
                       L.tile_prefix, r.max_bands, L.hdr, st));
+    return MP_OK;
+}
+
+// persistent join over the open bands -> [fragile pairs exactly] -> finalize
+mp_status execute_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
+                       const DeviceInfo *dev, cudaStream_t st)
+{
     const int bps = t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant];
     if (bps <= 0) return MP_EUNSUPPORTED;
     const int grid = dev->sms * bps;
@@ -196,6 +204,14 @@ mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long l
                               dev->sms * 8, st));
     MP_CU(launch_finalize(L.fins, r.nfin, max_fin_len, t.fp64, t.refine ? 1 : 0, st));
     return MP_OK;
+}
+
+mp_status run_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
+                   const DeviceInfo *dev, cudaStream_t st)
+{
+    const mp_status s = prepare_join(L, r, t, max_fin_len, st);
+    if (s != MP_OK) return s;
+    return execute_join(L, r, t, max_fin_len, dev, st);
 }
 
 bool valid_dtype(int32_t dtype) { return dtype == MP_F32 || dtype == MP_F64; }
@@ -370,6 +386,61 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
     return run_join(L, r, t, n - m + 1, d, st);
+}
+
+size_t mp_anytime_workspace_bytes(int64_t n, const mp_config *cfg)
+{
+    return mp_selfjoin_workspace_bytes(n, cfg);
+}
+
+mp_status mp_anytime_begin(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
+                           uint64_t seed, void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!x || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const int32_t m = cfg->m;
+    if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    const LayoutReq r = self_req(n, m, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(cudaMemsetAsync(L.hdr, 0, 256, st));
+    MP_CU(launch_convert(x, dtype, n, L.x64, L.hdr, st));
+    FamilyParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.kind = 0; F.m = m; F.fp64 = t.fp64; F.x64 = L.x64; F.n = n; F.ez = cfg->ez; F.flags = cfg->flags;
+    F.mu = L.mu; F.inv = L.inv; F.s32 = L.s32; F.s64 = L.s64; F.flat = L.flat; F.keys = L.keys;
+    F.mp_a = nullptr; F.pi_a = nullptr; F.out_stride = 0;   // outputs bound per run
+    F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
+    MP_CU(launch_family_descs(F, st));
+    if ((s = prepare_join(L, r, t, n - m + 1, st)) != MP_OK) return s;
+    MP_CU(launch_permute_bands(seed, L.bands, L.tile_prefix, L.scratch, r.max_bands, L.hdr, st));
+    return MP_OK;
+}
+
+mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, double *mp,
+                         int64_t *pi, void *ws, size_t ws_bytes, void *stream)
+{
+    TileCfg t;
+    if (!mp || !pi || !ws || !aligned256(ws) || !(fraction >= 0.0 && fraction <= 1.0))
+        return MP_EINVAL;
+    mp_status s = resolve(cfg, &t);
+    if (s != MP_OK) return s;
+    const int32_t m = cfg->m;
+    if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
+    const LayoutReq r = self_req(n, m, t);
+    const Layout L = carve(ws, r);
+    if (ws_bytes < L.bytes) return MP_ENOMEM;
+    const DeviceInfo *d = nullptr;
+    if ((s = current_device(&d)) != MP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    MP_CU(launch_bind_outputs(L.fins, mp, (long long *)pi, st));
+    MP_CU(launch_anytime_window(fraction, L.tile_prefix, L.hdr, st));
+    return execute_join(L, r, t, n - m + 1, d, st);
 }
 
 size_t mp_fluss_workspace_bytes(int64_t l)

@@ -110,6 +110,21 @@ __global__ void finalize_kernel(const FinDesc *__restrict__ fins, int refine)
 
 }  // namespace
 
+namespace {
+// anytime runs write their outputs where the caller says, per run
+__global__ void bind_outputs_kernel(FinDesc *fins, double *mp, long long *pi)
+{
+    fins[0].mp = mp;
+    fins[0].pi = pi;
+}
+}  // namespace
+
+cudaError_t launch_bind_outputs(FinDesc *fins, double *mp, long long *pi, cudaStream_t st)
+{
+    bind_outputs_kernel<<<1, 1, 0, st>>>(fins, mp, pi);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const FinDesc *fins, int nfin, long long max_len, int fp64,
                             int refine, cudaStream_t st)
 {

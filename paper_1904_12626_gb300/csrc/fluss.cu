@@ -24,6 +24,7 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;                       // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kSegBlocks = 1216;                   // boundary search: partial minima
 
 __global__ void arc_marks_kernel(const int64_t *__restrict__ pi, long long l, int *marks,
                                  unsigned *status)
@@ -135,62 +136,80 @@ __global__ void __launch_bounds__(kScanThreads) cac_kernel(const int *__restrict
     }
 }
 
-// num_segments rounds of (argmin, mask a zone around it), one block
-__global__ void __launch_bounds__(1024) segments_kernel(const double *__restrict__ cac, long long l,
-                                                        int num_segments, long long seg_excl,
-                                                        double *work, int64_t *segments)
+constexpr int kSegThreads = 256;
+
+// lowest index wins a tie; -1 (no candidate) loses to anything
+__device__ __forceinline__ bool seg_better(double v, long long i, double bv, long long bi)
 {
-    __shared__ double s_v[32];
-    __shared__ long long s_i[32];
-    __shared__ long long s_pick;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long q = threadIdx.x; q < l; q += blockDim.x) work[q] = cac[q];
-    __syncthreads();
-    for (int seg = 0; seg < num_segments; ++seg) {
-        double bv = INFINITY;
-        long long bi = -1;
-        for (long long q = threadIdx.x; q < l; q += blockDim.x) {
-            const double w = work[q];
-            if (w < bv) {                            // q increases: first minimum kept
-                bv = w;
-                bi = q;
-            }
+    return i >= 0 && (bi < 0 || v < bv || (v == bv && i < bi));
+}
+
+// one boundary search, pass 1: per-block minimum of cac over the positions
+// not within seg_excl of an earlier boundary (each element checks them all:
+// there are few)
+__global__ void __launch_bounds__(kSegThreads) seg_partial_kernel(const double *__restrict__ cac,
+                                                                  long long l, const int64_t *segments,
+                                                                  int s, long long seg_excl,
+                                                                  double *pv, long long *pidx)
+{
+    __shared__ double s_v[kSegThreads / 32];
+    __shared__ long long s_i[kSegThreads / 32];
+    double bv = INFINITY;
+    long long bi = -1;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < l;
+         q += (long long)gridDim.x * blockDim.x) {
+        bool masked = false;
+        for (int t = 0; t < s; ++t) {
+            const long long b = segments[t];
+            if (b < 0) continue;
+            const long long d = q > b ? q - b : b - q;
+            masked |= (d < seg_excl) || (d == 0);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov < bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
-                bv = ov;
-                bi = oi;
-            }
+        if (masked) continue;
+        const double v = cac[q];
+        if (seg_better(v, q, bv, bi)) {
+            bv = v;
+            bi = q;
         }
-        if (lane == 0) {
-            s_v[warp] = bv;
-            s_i[warp] = bi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double v = INFINITY;
-            long long b = -1;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                if (s_v[w] < v || (s_v[w] == v && s_i[w] >= 0 && (b < 0 || s_i[w] < b))) {
-                    v = s_v[w];
-                    b = s_i[w];
-                }
-            s_pick = b;
-            segments[seg] = b;
-        }
-        __syncthreads();
-        const long long b = s_pick;
-        if (b >= 0) {
-            const long long lo = b - seg_excl + 1 > 0 ? b - seg_excl + 1 : 0;
-            const long long hi = b + seg_excl < l ? b + seg_excl : l;
-            for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) work[q] = INFINITY;
-            if (threadIdx.x == 0) work[b] = INFINITY;
-        }
-        __syncthreads();
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (seg_better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        s_v[warp] = bv;
+        s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kSegThreads / 32; ++w)
+            if (seg_better(s_v[w], s_i[w], bv, bi)) {
+                bv = s_v[w];
+                bi = s_i[w];
+            }
+        pv[blockIdx.x] = bv;
+        pidx[blockIdx.x] = bi;
+    }
+}
+
+// pass 2: the minimum over the blocks is boundary s
+__global__ void seg_pick_kernel(const double *pv, const long long *pidx, int nblocks,
+                                int64_t *segments, int s)
+{
+    double bv = INFINITY;
+    long long bi = -1;
+    for (int b = 0; b < nblocks; ++b)
+        if (seg_better(pv[b], pidx[b], bv, bi)) {
+            bv = pv[b];
+            bi = pidx[b];
+        }
+    segments[s] = bi;
 }
 
 }  // namespace
@@ -200,7 +219,7 @@ size_t fluss_workspace_bytes(long long l)
     const long long ntiles = (l + kScanTile - 1) / kScanTile;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return up(256) + up(sizeof(int) * (size_t)(l + 1)) + up(sizeof(int) * (size_t)(ntiles + 1)) +
-           up(sizeof(double) * (size_t)(l > 0 ? l : 1));
+           up(16 * (size_t)kSegBlocks);
 }
 
 cudaError_t launch_fluss(const int64_t *pi, long long l, long long edge, int num_segments,
@@ -226,8 +245,17 @@ cudaError_t launch_fluss(const int64_t *pi, long long l, long long edge, int num
     tile_sums_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(marks, l, tile);
     tile_offsets_kernel<<<1, kScanThreads, 0, st>>>(tile, (int)ntiles);
     cac_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(marks, tile, l, edge, cac);
-    if (num_segments > 0 && segments)
-        segments_kernel<<<1, 1024, 0, st>>>(cac, l, num_segments, seg_excl, work, segments);
+    if (num_segments > 0 && segments) {
+        long long nblk = (l + kSegThreads - 1) / kSegThreads;
+        if (nblk > kSegBlocks) nblk = kSegBlocks;
+        double *pv = work;
+        long long *pidx = reinterpret_cast<long long *>(work + kSegBlocks);
+        for (int sg = 0; sg < num_segments; ++sg) {
+            seg_partial_kernel<<<(unsigned)nblk, kSegThreads, 0, st>>>(cac, l, segments, sg,
+                                                                     seg_excl, pv, pidx);
+            seg_pick_kernel<<<1, 1, 0, st>>>(pv, pidx, (int)nblk, segments, sg);
+        }
+    }
     return cudaGetLastError();
 }
 

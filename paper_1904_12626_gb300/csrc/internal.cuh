@@ -51,10 +51,13 @@ struct Hdr {
     unsigned int status;                  // first device-side mp_status != MP_OK
     unsigned int pad0;
     unsigned long long ticket;            // tile ticket counter of the persistent kernel
-    int nbands;                           // number of bands written by the planner
+    int nbands;                           // bands the tile kernel may take (a prefix of the
+                                          // band order; all of them unless anytime)
     int pad1;
     unsigned long long ntiles;            // number of tiles (same as tile_prefix[nbands])
     unsigned long long frag_count;        // fragile windows found (FP32-mixed path)
+    long long band_total;                 // anytime: bands planned
+    long long band_done;                  // anytime: bands processed so far
 };
 
 struct StatSet {
@@ -209,6 +212,13 @@ cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, do
 cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
                         long long *band_off, Band *bands, unsigned long long *tile_prefix,
                         long long max_bands, Hdr *hdr, cudaStream_t st);
+// anytime self-join: put the bands in a seeded random order (splitmix64,
+// Fisher-Yates) and open the window of bands [done, ceil(fraction * total))
+cudaError_t launch_permute_bands(unsigned long long seed, Band *bands,
+                                 unsigned long long *tile_prefix, long long *scratch,
+                                 long long max_bands, Hdr *hdr, cudaStream_t st);
+cudaError_t launch_anytime_window(double fraction, const unsigned long long *tile_prefix,
+                                  Hdr *hdr, cudaStream_t st);
 cudaError_t launch_family_descs(const FamilyParams &F, cudaStream_t st);
 cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int B, double ez,
                                  unsigned flags, int fp64, const double *x64, double *mu,
@@ -232,6 +242,7 @@ cudaError_t launch_join_f64(int v, const Prob *probs, const Band *bands,
 int f64_blocks_per_sm(int v);
 
 // finalize.cu
+cudaError_t launch_bind_outputs(FinDesc *fins, double *mp, long long *pi, cudaStream_t st);
 cudaError_t launch_finalize(const FinDesc *fins, int nfin, long long max_len, int fp64,
                             int refine, cudaStream_t st);
 

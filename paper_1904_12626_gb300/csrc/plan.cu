@@ -97,6 +97,73 @@ __global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, i
     }
 }
 
+// splitmix64 (Steele, Lea and Flood, 2014): the state advances by the golden
+// ratio constant and each output is a bijective mix of the state
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long &state)
+{
+    state += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Reorder the planned bands: slot s takes band perm[s], perm a Fisher-Yates
+// shuffle of 0..nb-1 (for i = nb-1 .. 1: swap perm[i] and perm[r % (i+1)],
+// r the next splitmix64 output), then rebuild the tile prefix in slot order.
+__global__ void permute_bands_kernel(unsigned long long seed, Band *bands,
+                                     unsigned long long *tile_prefix, long long *scratch,
+                                     long long max_bands, Hdr *hdr)
+{
+    const long long nb = hdr->nbands;
+    long long *perm = scratch;                             // [0, nb)
+    Band *old = reinterpret_cast<Band *>(scratch + max_bands);   // [0, nb)
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(old + max_bands);
+    if (threadIdx.x == 0) {
+        for (long long s = 0; s < nb; ++s) perm[s] = s;
+        unsigned long long st = seed;
+        for (long long i = nb - 1; i >= 1; --i) {
+            const long long j = (long long)(splitmix64(st) % (unsigned long long)(i + 1));
+            const long long t = perm[i];
+            perm[i] = perm[j];
+            perm[j] = t;
+        }
+    }
+    __syncthreads();
+    for (long long s = threadIdx.x; s < nb; s += blockDim.x) {
+        old[s] = bands[s];
+        cnt[s] = tile_prefix[s + 1] - tile_prefix[s];
+    }
+    __syncthreads();
+    for (long long s = threadIdx.x; s < nb; s += blockDim.x) {
+        bands[s] = old[perm[s]];
+        tile_prefix[s] = cnt[perm[s]];
+    }
+    __syncthreads();
+    block_exclusive_scan<unsigned long long>(tile_prefix, nb);
+    if (threadIdx.x == 0) {
+        hdr->band_total = nb;
+        hdr->band_done = 0;
+        hdr->nbands = 0;                                   // nothing open yet
+        hdr->ticket = 0ull;
+        hdr->ntiles = 0ull;
+    }
+}
+
+__global__ void anytime_window_kernel(double fraction, const unsigned long long *tile_prefix,
+                                      Hdr *hdr)
+{
+    const long long total = hdr->band_total;
+    const long long s0 = hdr->band_done;
+    long long s1 = (long long)ceil(fraction * (double)total);
+    if (s1 > total) s1 = total;
+    if (s1 < s0) s1 = s0;
+    hdr->ticket = tile_prefix[s0];
+    hdr->nbands = (int)s1;
+    hdr->ntiles = tile_prefix[s1];
+    hdr->band_done = s1;
+}
+
 }  // namespace
 
 cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
@@ -355,6 +422,25 @@ cudaError_t launch_batched_descs(const int64_t *offsets, const int32_t *ms, int 
         offsets, ms, B, ez, flags, fp64, x64, mu, inv, s32, s64, flat, (char *)keys, mp, pi,
         out_offsets,
         sets, probs, fins, hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace mpgb
+
+namespace mpgb {
+
+cudaError_t launch_permute_bands(unsigned long long seed, Band *bands,
+                                 unsigned long long *tile_prefix, long long *scratch,
+                                 long long max_bands, Hdr *hdr, cudaStream_t st)
+{
+    permute_bands_kernel<<<1, 1024, 0, st>>>(seed, bands, tile_prefix, scratch, max_bands, hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_anytime_window(double fraction, const unsigned long long *tile_prefix,
+                                  Hdr *hdr, cudaStream_t st)
+{
+    anytime_window_kernel<<<1, 1, 0, st>>>(fraction, tile_prefix, hdr);
     return cudaGetLastError();
 }
 

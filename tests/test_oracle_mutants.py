@@ -35,6 +35,8 @@ MUTANTS = {
     "arc_end_inclusive": ("if (a <= k && k < b) ++c;", "if (a <= k && k <= b) ++c;"),
     "iac_scale": ("double iac = 2.0 * (double)k * (double)(l - k) / (double)l;",
                   "double iac = 1.0 * (double)k * (double)(l - k) / (double)l;"),
+    "diag_mask_signed": ("if (J->diag_ok && !J->diag_ok[d]) return 0;",
+                         "if (J->diag_ok && !J->diag_ok[j > i ? j - i : 0]) return 0;"),
     "lr_sides_swapped": ("if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;",
                          "if ((J->side > 0 && j >= i) || (J->side < 0 && j <= i)) return 0;"),
 }

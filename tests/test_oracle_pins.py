@@ -50,7 +50,7 @@ def test_paper_printed_sizes():
     assert oracle.exclusion_zone(50, 0.25) == 13
 
 
-def _scipy_profile(x, m, excl=None, inclusive=False, y=None, side=0):
+def _scipy_profile(x, m, excl=None, inclusive=False, y=None, side=0, diag_ok=None):
     """MP/PI by scipy: z-normalise every window (population std), full
     Euclidean distance matrix, mask, row minimum.  Flat windows follow the
     stated convention (distance sqrt(2m) to everything).  side = -1 / +1
@@ -76,6 +76,8 @@ def _scipy_profile(x, m, excl=None, inclusive=False, y=None, side=0):
             bad |= jj >= ii
         elif side > 0:
             bad |= jj <= ii
+        if diag_ok is not None:
+            bad |= ~np.asarray(diag_ok, bool)[np.abs(ii - jj)]
         D[bad] = np.inf
     pi = np.argmin(D, axis=1)
     mp = D[np.arange(len(D)), pi]
@@ -198,6 +200,37 @@ def test_selfjoin_lr_against_scipy_bruteforce(n, m, ez, inclusive, seed):
     np.testing.assert_array_equal(np.minimum(ml, mr), mp)
     take_left = ml <= mr
     np.testing.assert_array_equal(np.where(take_left, pl, pr), pi)
+
+
+def test_selfjoin_diags_against_scipy_and_special_cases():
+    """An anytime run's best-so-far over a set of diagonals (Sec. 3.3.1,
+    3.3.3): scipy with the same mask; every diagonal allowed is the self-join;
+    one diagonal k gives min(d(i, i+k), d(i, i-k))."""
+    x = synth.random_walk(260, seed=17)
+    m = 8
+    l = len(x) - m + 1
+    E = oracle.exclusion_zone(m)
+    rng = np.random.default_rng(18)
+    ok = rng.random(l) < 0.3
+    mp, pi, _ = oracle.selfjoin_diags(x, m, ok)
+    mp_s, pi_s, gap = _scipy_profile(x, m, E, diag_ok=ok)
+    np.testing.assert_array_equal(np.isinf(mp), np.isinf(mp_s))
+    fin = np.isfinite(mp_s)
+    np.testing.assert_allclose(mp[fin], mp_s[fin], atol=1e-10)
+    sep = fin & (gap > 1e-9)
+    np.testing.assert_array_equal(pi[sep], pi_s[sep])
+    full = oracle.selfjoin(x, m)
+    allm = oracle.selfjoin_diags(x, m, np.ones(l, bool))
+    np.testing.assert_array_equal(allm[0], full[0])
+    np.testing.assert_array_equal(allm[1], full[1])
+    k = 37
+    one = np.zeros(l, bool)
+    one[k] = True
+    mp1, pi1, _ = oracle.selfjoin_diags(x, m, one)
+    for i in range(l):
+        cands = [j for j in (i - k, i + k) if 0 <= j < l]
+        ds = [oracle.distance(x, m, i, j) for j in cands]
+        assert mp1[i] == min(ds) and pi1[i] == cands[int(np.argmin(ds))]
 
 
 def test_abjoin_against_scipy_bruteforce():
