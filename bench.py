@@ -28,6 +28,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -35,6 +37,7 @@ if ROOT not in sys.path:
 METRIC = "self-join Gcells/s @n=2^20,m=256: FP32-mixed vs FP64 GPU; % FP32 peak"
 # --join lr: the same workload through the left/right-profile entry point
 METRIC_LR = "left/right self-join Gcells/s @n=2^20,m=256 (FP32-mixed)"
+METRIC_RAW = "non-normalised self-join Gcells/s @n=2^20,m=256 (FP32-mixed, tonal signal)"
 METRIC_ANY = "anytime self-join, 5% run then resume to 100%, Gcells/s @n=2^20,m=256 (FP32-mixed)"
 N_DEFAULT, M_DEFAULT, SEED = 1 << 20, 256, 2024
 # DRAM traffic of one tile-kernel launch from an ncu capture, with the csrc digest it was taken at
@@ -215,10 +218,11 @@ def run_reference(args, world, rank):
 
 
 def config_block(args, E, cells):
-    kind = {"lr": "left/right self-join", "anytime": "anytime self-join (5% run, resume to 100%)"
-            }.get(getattr(args, "join", "self"), "self-join")
+    kind = {"lr": "left/right self-join", "anytime": "anytime self-join (5% run, resume to 100%)",
+            "raw": "non-normalised self-join"}.get(getattr(args, "join", "self"), "self-join")
+    data = "tonal signal (synth.tonal)" if getattr(args, "join", "self") == "raw" else "planted random walk"
     prec = "FP32-mixed" if args.prec == "fp32" else "FP64"
-    return {"workload": f"{kind}, planted random walk n={args.n} float32, m={args.m}, ez=0.5 "
+    return {"workload": f"{kind}, {data} n={args.n} float32, m={args.m}, ez=0.5 "
                         f"(E={E}), {prec}", "n": args.n, "m": args.m, "cells": cells,
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
@@ -250,7 +254,12 @@ def run_ours(args, world, rank, local):
     build.build()
     api.init()
     lib = _lib.load()
-    x_np, info = workload(args.n, args.m)
+    raw = args.join == "raw"
+    if raw:                         # the non-normalised distance's domain: a bounded signal
+        from paper_1904_12626_gb300 import synth
+        x_np = synth.tonal(args.n, seed=SEED, dtype=np.float32)
+    else:
+        x_np, info = workload(args.n, args.m)
     n, m = args.n, args.m
     E = math.ceil(0.5 * m)
     l = n - m + 1
@@ -258,7 +267,7 @@ def run_ours(args, world, rank, local):
     x = torch.from_numpy(x_np).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     import ctypes
-    cfg = _lib.make_config(m, 0.5, args.prec)
+    cfg = _lib.make_config(m, 0.5, args.prec, flags=_lib.MP_FLAG_RAW if raw else 0)
     lr = args.join == "lr"
     anytime = args.join == "anytime"
     need = (lib.mp_selfjoin_lr_workspace_bytes if lr else lib.mp_selfjoin_workspace_bytes)(
@@ -274,7 +283,7 @@ def run_ours(args, world, rank, local):
             run = api.Anytime(xx, m, seed=1, prec=prec, ws=ws)
             run.run(0.05)
             return run.run(1.0)
-        return api.selfjoin(xx, m, 0.5, prec, ws=ws)
+        return api.selfjoin(xx, m, 0.5, prec, raw=raw, ws=ws)
 
     def step(prec):
         return join(x, prec)
@@ -320,7 +329,7 @@ def run_ours(args, world, rank, local):
 
     # all-FP64 kernel on the same input (comparison leg, one warm-up + timed steps)
     fp64 = None
-    if not args.skip_fp64 and not lr and not anytime:
+    if not args.skip_fp64 and not lr and not anytime and not raw:
         cfg64 = _lib.make_config(m, 0.5, "fp64")
         ws64 = api.workspace(lib.mp_selfjoin_workspace_bytes(n, ctypes.byref(cfg64)), x.device)
         api.selfjoin(x, m, 0.5, "fp64", ws=ws64)
@@ -373,13 +382,15 @@ def run_ours(args, world, rank, local):
     cells_per_s_kernel = cells / (kernel_ms / 1e3)
     achieved = 6 * cells_per_s_kernel / 1e12
     line = {
-        "metric": METRIC_LR if lr else (METRIC_ANY if anytime else METRIC), "value": value, "unit": "Gcells/s", "n_gpus": world,
+        "metric": (METRIC_LR if lr else METRIC_ANY if anytime else METRIC_RAW if raw else METRIC),
+        "value": value, "unit": "Gcells/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)",
         "data": "synthetic", "config": config_block(args, E, cells),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
-                     "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
+                     "unit": ("T FP32 lane-instructions/s (6 per cell: 2 FFMA, "
+                              f"{'2 FADD' if raw else '2 FMUL'}, 2 FSETP)"),
                      "frac": achieved / issue_peak, "traffic": None if lr else traffic_from_profile(),
                      "kernel": kernel_name, "kernel_ms": kernel_ms,
                      "peak_basis": f"{sms} SMs x 128 lanes x {f_max:.0f} MHz "
@@ -495,7 +506,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
-    ap.add_argument("--join", choices=("self", "lr", "anytime", "fluss"), default="self")
+    ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss"), default="self")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--m", type=int, default=M_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=1)

@@ -65,6 +65,10 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
 #define MP_FLAG_NO_REFINE      0x2u   /* MP from the kernel's correlation instead of
                                          the exact FP64 distance of (i, PI[i]) */
 #define MP_FLAG_PAN_NORMALIZE  0x4u   /* mp_pan: divide each row by sqrt(2m) */
+#define MP_FLAG_RAW            0x8u   /* non-normalised Euclidean distance (SiMPle,
+                                         Sec. 3.3.4): d = ||x_i - x_j||, no
+                                         z-normalisation, no flat-window rule;
+                                         mp_selfjoin, mp_selfjoin_lr, mp_abjoin */
 
 /*
  * Join parameters.  m: window length (>= 4).  ez: exclusion-zone fraction

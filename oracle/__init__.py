@@ -79,6 +79,10 @@ def _bind(lib):
     lib.oracle_selfjoin_diags.argtypes = [_d, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_int, _u8, _i64, ctypes.c_int64, _d, _i64, _d,
                                           ctypes.c_int]
+    lib.oracle_join_raw.restype = ctypes.c_int
+    lib.oracle_join_raw.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_int, _i64,
+                                    ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
     lib.oracle_abjoin.restype = ctypes.c_int
     lib.oracle_abjoin.argtypes = [_d, ctypes.c_int64, _d, ctypes.c_int64, ctypes.c_int32,
                                   _i64, ctypes.c_int64, _d, _i64, _d, ctypes.c_int]
@@ -251,6 +255,27 @@ def selfjoin_diags(x, m: int, diag_ok, ez: float = 0.5, rows=None, inclusive: bo
                                    _p(sec, _d), nthreads)
     if rc != 0:
         raise ValueError(f"oracle_selfjoin_diags failed ({rc})")
+    return mp, pi, sec
+
+
+def join_raw(a, m: int, b=None, ez: float = 0.5, rows=None, inclusive: bool = False,
+             nthreads: int = 0, lib=None):
+    """Brute force with the non-normalised distance ||x_i - x_j||: a self-join
+    of a (exclusion zone ez), or an AB-join of a against b.  Returns (mp, pi, second)."""
+    lib = lib or load()
+    a = _f64(a)
+    bb = a if b is None else _f64(b)
+    la = profile_length(len(a), m, lib)
+    rows = np.arange(la, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    excl = exclusion_zone(m, ez, lib)
+    mp = np.empty(len(rows))
+    pi = np.empty(len(rows), dtype=np.int64)
+    sec = np.empty(len(rows))
+    rc = lib.oracle_join_raw(_p(a, _d), len(a), _p(bb, _d), len(bb), m, int(b is not None), excl,
+                             int(inclusive), _p(rows, _i64), len(rows), _p(mp, _d), _p(pi, _i64),
+                             _p(sec, _d), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle_join_raw failed ({rc})")
     return mp, pi, sec
 
 

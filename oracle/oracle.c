@@ -193,6 +193,7 @@ typedef struct {
     int self;              /* 1: self-join, apply the exclusion zone */
     int side;              /* self-join: 0 any j, -1 only j < i, +1 only j > i */
     const uint8_t *diag_ok; /* self-join: nullable; j allowed only if diag_ok[|i - j|] */
+    int raw;               /* 1: non-normalised distance ||x_i - x_j|| (no z-norm, no flat rule) */
     int64_t excl;
     int inclusive;
     const int64_t *rows;
@@ -233,7 +234,14 @@ static void *join_worker(void *arg)
         for (int64_t j = 0; j < J->lc; ++j) {
             if (!admissible(J, i, j)) continue;
             double d;
-            if (fi || J->cflat[j]) {
+            if (J->raw) {
+                double acc = 0.0;
+                for (int32_t k = 0; k < m; ++k) {
+                    double e = J->xr[i + k] - J->xc[j + k];
+                    acc += e * e;
+                }
+                d = sqrt(acc);
+            } else if (fi || J->cflat[j]) {
                 d = flatd;
             } else {
                 znorm(J->xc, m, j, J->cmu[j], J->csig[j], zj);
@@ -353,6 +361,28 @@ int oracle_selfjoin_diags(const double *x, int64_t n, int32_t m, int64_t excl, i
     job_t J = {0};
     J.xr = x; J.xc = x; J.lr = l; J.lc = l; J.m = m; J.self = 1; J.diag_ok = diag_ok;
     J.excl = excl; J.inclusive = inclusive;
+    J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
+    return run_join(&J, nthreads);
+}
+
+/*
+ * Non-normalised distance (SiMPle, Sec. 3.3.4: no z-normalisation):
+ * d(i,j) = ||x_i - x_j||, the plain Euclidean distance of the raw windows.
+ * Self-join with the exclusion zone (raw_ab = 0) or AB-join (raw_ab = 1, b
+ * the candidate series).  No flat-window rule applies.
+ */
+int oracle_join_raw(const double *a, int64_t na, const double *b, int64_t nb, int32_t m,
+                    int raw_ab, int64_t excl, int inclusive, const int64_t *rows, int64_t nrows,
+                    double *mp, int64_t *pi, double *second, int nthreads)
+{
+    int64_t la = oracle_profile_length(na, m);
+    int64_t lb = raw_ab ? oracle_profile_length(nb, m) : la;
+    if (la <= 0 || lb <= 0 || m < 2) return -1;
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= la) return -1;
+    job_t J = {0};
+    J.xr = a; J.xc = raw_ab ? b : a; J.lr = la; J.lc = lb; J.m = m; J.self = !raw_ab;
+    J.raw = 1; J.excl = excl; J.inclusive = inclusive;
     J.rows = rows; J.nrows = nrows; J.mp = mp; J.pi = pi; J.second = second;
     return run_join(&J, nthreads);
 }

@@ -19,6 +19,7 @@ MP_PREC_FP64, MP_PREC_FP32_MIXED = 0, 1
 MP_FLAG_EXCL_INCLUSIVE = 0x1
 MP_FLAG_NO_REFINE = 0x2
 MP_FLAG_PAN_NORMALIZE = 0x4
+MP_FLAG_RAW = 0x8
 
 
 class MPConfig(ctypes.Structure):

@@ -74,12 +74,15 @@ def stats(x: torch.Tensor, m: int, stream=None):
 
 
 def selfjoin(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *, refine: bool = True,
-             inclusive: bool = False, tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
-             ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
-    """Self-join matrix profile of one series.  Returns (mp float64, pi int64)."""
+             inclusive: bool = False, raw: bool = False, tile_rows: int = 0, anchor_every: int = 0,
+             variant: int = 0, ws: torch.Tensor | None = None, stream=None,
+             check_status: bool = False):
+    """Self-join matrix profile of one series.  Returns (mp float64, pi int64).
+    raw=True: the non-normalised distance ||x_i - x_j|| (SiMPle)."""
     x = _prep(x, "x")
     lib = _lib.load()
-    flags = (0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_EXCL_INCLUSIVE if inclusive else 0)
+    flags = ((0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_EXCL_INCLUSIVE if inclusive else 0)
+             | (_lib.MP_FLAG_RAW if raw else 0))
     cfg = make_config(m, ez, prec, anchor_every, tile_rows, variant, flags)
     n = x.numel()
     l = n - m + 1
@@ -98,14 +101,15 @@ def selfjoin(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *, re
 
 
 def selfjoin_lr(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *,
-                refine: bool = True, inclusive: bool = False, tile_rows: int = 0,
-                anchor_every: int = 0, variant: int = 0, ws: torch.Tensor | None = None,
-                stream=None, check_status: bool = False):
+                refine: bool = True, inclusive: bool = False, raw: bool = False,
+                tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
+                ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
     """Left and right self-join profiles.  Returns (mp_left, pi_left, mp_right, pi_right):
     the nearest neighbour of each window among the windows before / after it."""
     x = _prep(x, "x")
     lib = _lib.load()
-    flags = (0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_EXCL_INCLUSIVE if inclusive else 0)
+    flags = ((0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_EXCL_INCLUSIVE if inclusive else 0)
+             | (_lib.MP_FLAG_RAW if raw else 0))
     cfg = make_config(m, ez, prec, anchor_every, tile_rows, variant, flags)
     n = x.numel()
     l = n - m + 1
@@ -185,8 +189,9 @@ def fluss(pi: torch.Tensor, m: int, num_segments: int = 2, *, edge: int | None =
 
 
 def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refine: bool = True,
-           both: bool = True, tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
-           ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
+           both: bool = True, raw: bool = False, tile_rows: int = 0, anchor_every: int = 0,
+           variant: int = 0, ws: torch.Tensor | None = None, stream=None,
+           check_status: bool = False):
     """AB-join.  Returns (mp_a, pi_a, mp_b, pi_b); the B side is None unless `both`."""
     a = _prep(a, "a")
     b = _prep(b, "b")
@@ -194,7 +199,7 @@ def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refi
         raise TypeError("a and b must share a dtype")
     lib = _lib.load()
     cfg = make_config(m, 0.5, prec, anchor_every, tile_rows, variant,
-                      0 if refine else _lib.MP_FLAG_NO_REFINE)
+                      (0 if refine else _lib.MP_FLAG_NO_REFINE) | (_lib.MP_FLAG_RAW if raw else 0))
     na, nb = a.numel(), b.numel()
     la, lb = na - m + 1, nb - m + 1
     if m < 4 or la < 1 or lb < 1:

@@ -24,6 +24,7 @@ struct DeviceInfo {
     int sms = 0;
     int f32_bps[8] = {0};
     int f64_bps[8] = {0};
+    int f32_raw_bps = 0, f64_raw_bps = 0;       // MP_FLAG_RAW kernels (variant 0 shape)
 };
 DeviceInfo g_dev[kMaxDevices];
 std::mutex g_mu;
@@ -46,6 +47,8 @@ mp_status device_info(int dev, const DeviceInfo **out)
             if (cur != dev) cudaSetDevice(dev);
             for (int v = 0; v < f32_variant_count() && v < 8; ++v) d.f32_bps[v] = f32_blocks_per_sm(v);
             for (int v = 0; v < f64_variant_count() && v < 8; ++v) d.f64_bps[v] = f64_blocks_per_sm(v);
+            d.f32_raw_bps = f32_raw_blocks_per_sm();
+            d.f64_raw_bps = f64_raw_blocks_per_sm();
             if (cur != dev && cur >= 0) cudaSetDevice(cur);
         }
         d.ready = true;
@@ -72,6 +75,7 @@ struct TileCfg {
     int tile_rows;
     int anchor_every;
     bool refine;
+    bool raw;                // MP_FLAG_RAW: non-normalised distance (variant 0 only)
 };
 
 mp_status resolve(const mp_config *cfg, TileCfg *t)
@@ -93,6 +97,8 @@ mp_status resolve(const mp_config *cfg, TileCfg *t)
     t->anchor_every = cfg->anchor_every > 0 ? (int)(ceil_div(cfg->anchor_every, rc) * rc) : 0;
     if (t->anchor_every >= tr) t->anchor_every = 0;
     t->refine = (cfg->flags & MP_FLAG_NO_REFINE) == 0;
+    t->raw = (cfg->flags & MP_FLAG_RAW) != 0;
+    if (t->raw && t->variant != 0) return MP_EUNSUPPORTED;
     return MP_OK;
 }
 
@@ -184,13 +190,20 @@ mp_status prepare_join(const Layout &L, const LayoutReq &r, const TileCfg &t, lo
 mp_status execute_join(const Layout &L, const LayoutReq &r, const TileCfg &t, long long max_fin_len,
                        const DeviceInfo *dev, cudaStream_t st)
 {
-    const int bps = t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant];
+    const int bps = t.raw ? (t.fp64 ? dev->f64_raw_bps : dev->f32_raw_bps)
+                          : (t.fp64 ? dev->f64_bps[t.variant] : dev->f32_bps[t.variant]);
     if (bps <= 0) return MP_EUNSUPPORTED;
     const int grid = dev->sms * bps;
     DeviceInfo *dm = const_cast<DeviceInfo *>(dev);
     const bool timing = g_timing && dm->ev[0] != nullptr;
     if (timing) MP_CU(cudaEventRecord(dm->ev[0], st));
-    if (t.fp64)
+    if (t.raw && t.fp64)
+        MP_CU(launch_join_f64_raw(L.probs, L.bands, L.tile_prefix, L.hdr, t.tile_rows,
+                                  t.anchor_every, grid, st));
+    else if (t.raw)
+        MP_CU(launch_join_f32_raw(L.probs, L.bands, L.tile_prefix, L.hdr, t.tile_rows,
+                                  t.anchor_every, grid, st));
+    else if (t.fp64)
         MP_CU(launch_join_f64(t.variant, L.probs, L.bands, L.tile_prefix, L.hdr, t.tile_rows,
                               t.anchor_every, grid, st));
     else

@@ -43,6 +43,24 @@ __device__ __forceinline__ double exact_distance(const FinDesc &F, long long i, 
     return d > cap ? cap : d;
 }
 
+// non-normalised distance ||x_i - x_j|| in FP64 from the series
+__device__ __forceinline__ double exact_raw_distance(const FinDesc &F, long long i, long long j)
+{
+    const double *xr = F.xR + i, *xc = F.xC + j;
+    double a0 = 0.0, a1 = 0.0;
+    int t = 0;
+    for (; t + 1 < F.m; t += 2) {
+        const double d0 = xr[t] - xc[t], d1 = xr[t + 1] - xc[t + 1];
+        a0 = fma(d0, d0, a0);
+        a1 = fma(d1, d1, a1);
+    }
+    if (t < F.m) {
+        const double d0 = xr[t] - xc[t];
+        a0 = fma(d0, d0, a0);
+    }
+    return sqrt(a0 + a1);
+}
+
 template <bool FP64KEY>
 __device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long long l, int refine)
 {
@@ -84,7 +102,9 @@ __device__ __forceinline__ void finalize_one(const FinDesc &F, long long i, long
             }
         }
         if (have) {
-            if (refine) {
+            if (F.raw) {                         // key value: the score -d^2 / 2
+                mpv = refine ? exact_raw_distance(F, i, piv) : sqrt(rho < 0.0 ? -2.0 * rho : 0.0);
+            } else if (refine) {
                 mpv = exact_distance(F, i, piv, F.invR[i]);
             } else {
                 rho = rho > 1.0 ? 1.0 : (rho < -1.0 ? -1.0 : rho);

@@ -60,6 +60,14 @@ struct Hdr {
     long long band_done;                  // anytime: bands processed so far
 };
 
+// Non-normalised distance (raw = 1; SiMPle's distance, Sec. 3.3.4: no
+// z-normalisation): d(i,j)^2 = ||x_i - x_j||^2 = 2 h_i + 2 h_j - 2 q(i,j)
+// with q the raw dot product and h_i = ||x_i||^2 / 2.  The joins maximise the
+// score s(i,j) = q(i,j) - h_i - h_j = -d^2 / 2 instead of the correlation.
+// q follows the same recurrence as the centred product, q(i,j) = q(i-1,j-1)
+// + df_i dg_j + df_j dg_i, with df_i = (x_{i+m-1} - x_{i-1}) / 2 and
+// dg_i = x_{i+m-1} + x_{i-1}; the per-window arrays hold mu = 0 and h in the
+// slot of the inverse norm, and no window is flat or ill-conditioned.
 struct StatSet {
     const double *x;                      // FP64 series of this set
     long long n;                          // series length
@@ -70,7 +78,7 @@ struct StatSet {
     int partner;                          // set whose windows are this set's candidates
     int dir;                              // self-join candidates: 0 both sides, +1 only
                                           // j > i (right profile), -1 only j < i (left)
-    int pad;
+    int raw;                              // 1: non-normalised distance (see below)
 };
 
 // A window is "fragile" when its centred norm is below kFragileFactor times
@@ -93,7 +101,7 @@ struct Prob {
     long long nC;                         // column series length
     long long kmin, kmax;                 // inclusive diagonal range
     int m;
-    int pad;
+    int raw;                              // 1: non-normalised distance
 };
 
 struct Band {
@@ -118,6 +126,8 @@ struct FinDesc {
     double scale;                         // multiply MP by this (pan normalisation)
     int m;
     int dir;                              // as StatSet::dir (flat rows' closed-form PI)
+    int raw;                              // 1: non-normalised distance
+    int pad;
 };
 
 // Parameters of the descriptor kernel of a self-join (kind 0), an AB-join
@@ -234,12 +244,20 @@ cudaError_t launch_join_f32(int v, const Prob *probs, const Band *bands,
                             const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
                             int anchor_every, int grid, cudaStream_t st);
 int f32_blocks_per_sm(int v);
+int f32_raw_blocks_per_sm();
+cudaError_t launch_join_f32_raw(const Prob *probs, const Band *bands,
+                                const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                                int anchor_every, int grid, cudaStream_t st);
 int f64_variant_count();
 bool f64_variant_info(int v, int *tile_diags, int *chunk_rows, int *threads, int *smem);
 cudaError_t launch_join_f64(int v, const Prob *probs, const Band *bands,
                             const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
                             int anchor_every, int grid, cudaStream_t st);
 int f64_blocks_per_sm(int v);
+int f64_raw_blocks_per_sm();
+cudaError_t launch_join_f64_raw(const Prob *probs, const Band *bands,
+                                const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                                int anchor_every, int grid, cudaStream_t st);
 
 // finalize.cu
 cudaError_t launch_bind_outputs(FinDesc *fins, double *mp, long long *pi, cudaStream_t st);

@@ -5,15 +5,15 @@
 namespace mpgb {
 namespace {
 
-template <int D, int W, int RC, int MINB>
+template <int D, int W, int RC, int MINB, bool RAW = false>
 struct V {
     using Sh = TileShape<TraitsF64, D, W, RC>;
-    static void *fn() { return (void *)join_tile_kernel<TraitsF64, D, W, RC, MINB>; }
+    static void *fn() { return (void *)join_tile_kernel<TraitsF64, D, W, RC, MINB, RAW>; }
     static cudaError_t launch(const Prob *probs, const Band *bands,
                               const unsigned long long *tp, Hdr *hdr, int tile_rows,
                               int anchor_every, int grid, cudaStream_t st)
     {
-        join_tile_kernel<TraitsF64, D, W, RC, MINB><<<grid, Sh::NT, Sh::SMEM, st>>>(
+        join_tile_kernel<TraitsF64, D, W, RC, MINB, RAW><<<grid, Sh::NT, Sh::SMEM, st>>>(
             probs, bands, tp, hdr, tile_rows, anchor_every);
         return cudaGetLastError();
     }
@@ -79,6 +79,26 @@ cudaError_t launch_join_f64(int v, const Prob *probs, const Band *bands,
     default:
         return cudaErrorInvalidValue;
     }
+}
+
+// the non-normalised distance (MP_FLAG_RAW) runs variant 0's shape only
+int f64_raw_blocks_per_sm()
+{
+    using R = V<4, 4, 128, 2, true>;
+    int n = 0;
+    cudaFuncSetAttribute(R::fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, R::Sh::SMEM);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, R::fn(), R::Sh::NT, R::Sh::SMEM) !=
+        cudaSuccess)
+        n = 0;
+    return n;
+}
+
+cudaError_t launch_join_f64_raw(const Prob *probs, const Band *bands,
+                                const unsigned long long *tile_prefix, Hdr *hdr, int tile_rows,
+                                int anchor_every, int grid, cudaStream_t st)
+{
+    return V<4, 4, 128, 2, true>::launch(probs, bands, tile_prefix, hdr, tile_rows,
+                                                 anchor_every, grid, st);
 }
 
 }  // namespace mpgb

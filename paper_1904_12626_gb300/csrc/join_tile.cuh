@@ -229,22 +229,35 @@ static __device__ __noinline__ double exact_correlation(const Prob &P, long long
     double acc = acc0 + acc1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (P.raw) return (acc - P.rInv[i]) - P.cInv[j];      // mu = 0, inv = h: the score
     return acc * P.rInv[i] * P.cInv[j];
 }
 
-// running sums of a staged window's squared norm (1/invn^2), df^2, dg^2 and
-// a count (flat, fragile and padding entries skipped)
+// The value a cell is ranked by: the correlation c invn_i invn_j, or with
+// RAW (non-normalised distance) the score q - h_i - h_j = -d^2 / 2; z is the
+// stats lane holding invn (or h).
+template <bool RAW, class T>
+__device__ __forceinline__ T cell_score(T c, T zc, T zr)
+{
+    if constexpr (RAW) return (c - zc) - zr;
+    else return c * zc * zr;
+}
+
+// running sums of a staged window's squared norm (1/invn^2, or 2h with RAW),
+// df^2, dg^2 and a count (flat, fragile and padding entries skipped); with
+// RAW also the largest h (*hmax)
 constexpr float kBiasSigma = 2.0f;
 
-template <class S4>
-__device__ __forceinline__ void track_max(float *mx, const S4 &v)
+template <bool RAW, class S4>
+__device__ __forceinline__ void track_max(float *mx, float *hmax, const S4 &v)
 {
-    const float inv = (float)v.z;
-    if (inv > 0.f) {
-        mx[0] += 1.0f / (inv * inv);
+    const float z = (float)v.z;
+    if (RAW ? (z == z) : (z > 0.f)) {
+        mx[0] += RAW ? 2.0f * z : 1.0f / (z * z);
         mx[1] += (float)v.x * (float)v.x;
         mx[2] += (float)v.y * (float)v.y;
         mx[3] += 1.0f;
+        if (RAW) *hmax = fmaxf(*hmax, z);
     }
 }
 
@@ -263,7 +276,7 @@ struct CovArr {
 // the correlations are bit-identical), and merge every candidate that reaches
 // a row's or a column's threshold into the keys (FP64 path: the recurrence's
 // values are exact enough to go to the keys directly).
-template <class Tr, int D>
+template <class Tr, int D, bool RAW>
 __device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
                                           typename Tr::S4 *sCol, typename Tr::S4 *rS,
                                           typename Tr::S4 *cS, typename Tr::Key *rKey,
@@ -285,7 +298,7 @@ __device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
             const S4 cc = sCol[cpos<D>(lane_off + s + u + d)];
             c0.v[d] = Tr::fma_(rw.x, cc.y, c0.v[d]);
             c0.v[d] = Tr::fma_(cc.x, rw.y, c0.v[d]);
-            rho[d] = c0.v[d] * cc.z * rw.z;
+            rho[d] = cell_score<RAW>(c0.v[d], cc.z, rw.z);
             rowc[d] = rho[d] >= rw.w;
             colc[d] = rho[d] >= cc.w;
             any |= rowc[d] | colc[d];
@@ -415,7 +428,7 @@ constexpr int kItemsPerWarp = 32;
 // Exact comparisons take a second pass (rare).  The warp's column candidates
 // are then compacted through shared memory and merged one per lane, so a
 // group costs a few global round trips, not one per cell.
-template <int D>
+template <int D, bool RAW>
 __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, float4 *sCol,
                                                  float4 *rS, float4 *cS, Key128 *rKey,
                                                  Key128 *cKey, Hdr *hdr, CovArr<float, D> c0,
@@ -455,12 +468,12 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
             const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
             c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
             c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
-            U[d] = c0.v[d] * cc.z * rw.z;
+            U[d] = cell_score<RAW>(c0.v[d], cc.z, rw.z);
             if (U[d] >= cc.w) {
                 if (U[d] > aU[d]) {
                     a2[d] = aU[d];
                     aU[d] = U[d];
-                    aW[d] = 2.0f * ebias * cc.z * rw.z;
+                    aW[d] = RAW ? 2.0f * ebias : 2.0f * ebias * cc.z * rw.z;
                     au[d] = u;
                 } else if (U[d] > a2[d]) {
                     a2[d] = U[d];
@@ -479,7 +492,7 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
         if (top != 0ull) {                      // warp-uniform
             const long long jt = TraitsF32::pidx(top);
             const float czt = sCol[cpos<D>((int)(jt - r - k0))].z;
-            const float lt = TraitsF32::pval(top) - 2.0f * ebias * czt * rw.z;
+            const float lt = TraitsF32::pval(top) - (RAW ? 2.0f * ebias : 2.0f * ebias * czt * rw.z);
             bool band = false;
 #pragma unroll
             for (int d = 0; d < D; ++d)
@@ -544,7 +557,7 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
                 const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
                 c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
                 c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
-                const float Uc = c0.v[d] * cc.z * rw.z;
+                const float Uc = cell_score<RAW>(c0.v[d], cc.z, rw.z);
                 const int o = u + d;
                 const bool need_s = Uc >= lo_l[o];
                 const bool need_r = rb && Uc >= ltu;
@@ -649,7 +662,7 @@ constexpr int kQueue = 8;
 // thresholds).  The column stats walk through a D-entry register ring; the
 // row stats are a shared-memory broadcast.  Returns the number of groups
 // recorded in q_c0 / q_s for replay.
-template <class Tr, int D, int RC>
+template <class Tr, int D, int RC, bool RAW>
 static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, int s1,
                                                  int lane_off, CovArr<typename Tr::T, D> *q_c0,
                                                  int *q_s)
@@ -686,7 +699,7 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
                 const S4 &cc = cs[(d + u) % D];
                 c[d] = Tr::fma_(rw.x, cc.y, c[d]);
                 c[d] = Tr::fma_(cc.x, rw.y, c[d]);
-                const T rho = c[d] * cc.z * rw.z;
+                const T rho = cell_score<RAW>(c[d], cc.z, rw.z);
                 hit |= (rho >= rw.w);
                 hit |= (rho >= cc.w);
             }
@@ -715,7 +728,7 @@ struct TileShape {
 };
 
 // MINB: minimum resident CTAs per SM the register allocation must allow
-template <class Tr, int D, int W, int RC, int MINB>
+template <class Tr, int D, int W, int RC, int MINB, bool RAW>
 __global__ void __launch_bounds__(W * 32, MINB)
 join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                  const unsigned long long *__restrict__ tile_prefix, Hdr *hdr, int tile_rows,
@@ -737,8 +750,9 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                         (threadIdx.x >> 5) * kItemsPerWarp;
     __shared__ unsigned long long s_tile;
     // per-chunk sums of {norm^2, df^2, dg^2, count} over the staged rows and
-    // columns (two parity sets of 8): their RMS values size the error bias
-    __shared__ float s_mx[16];
+    // columns, and (RAW) the largest h of each (two parity sets of 12): they
+    // size the error bias
+    __shared__ float s_mx[24];
 
     const int lane = threadIdx.x & 31;
     const int lane_off = threadIdx.x * D;
@@ -751,7 +765,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_tile = atomicAdd(&hdr->ticket, 1ull);
-        if (threadIdx.x < 16) s_mx[threadIdx.x] = 0.0f;
+        if (threadIdx.x < 24) s_mx[threadIdx.x] = 0.0f;
         __syncthreads();
         const unsigned long long tile = s_tile;
         if (tile >= ntiles) break;
@@ -788,7 +802,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
         for (long long r = i0; r < i1; r += RC, ++chunk) {
             const int nrows = (int)min((long long)RC, i1 - r);
             const int nrr = (nrows + D - 1) / D * D;
-            const int par = (chunk & 1) * 8;
+            const int par = (chunk & 1) * 12;
             __syncthreads();
             // stage {df, dg, invn, thr} of the chunk's rows and columns: plain
             // copies (L2 reads, so thresholds raised by other CTAs are seen),
@@ -796,6 +810,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
             {
                 constexpr int U = 4;
                 float mx[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float hm[2] = {0.f, 0.f};
                 for (int t0 = threadIdx.x; t0 < nrr; t0 += NT * U) {
                     S4 v[U];
 #pragma unroll
@@ -805,7 +820,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     for (int k = 0; k < U; ++k)
                         if (t0 + k * NT < nrr) {
                             sRow[t0 + k * NT] = v[k];
-                            if (Tr::kBias) track_max(mx, v[k]);
+                            if (Tr::kBias) track_max<RAW>(mx, hm, v[k]);
                         }
                 }
                 const long long cb = r + k0;
@@ -819,7 +834,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     for (int k = 0; k < U; ++k)
                         if (t0 + k * NT < ncols) {
                             sCol[cpos<D>(t0 + k * NT)] = v[k];
-                            if (Tr::kBias) track_max(mx + 4, v[k]);
+                            if (Tr::kBias) track_max<RAW>(mx + 4, hm + 1, v[k]);
                         }
                 }
                 if (Tr::kBias) {                       // warp sums, then one add per warp
@@ -829,6 +844,18 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                         if (lane == 0 && v > 0.f) atomicAdd(&s_mx[par + k], v);
+                    }
+                    if (RAW) {                         // h >= 0: integer max on the bits
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            float v = hm[k];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1)
+                                v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                            if (lane == 0 && v > 0.f)
+                                atomicMax(reinterpret_cast<int *>(&s_mx[par + 8 + k]),
+                                          __float_as_int(v));
+                        }
                     }
                 }
             }
@@ -847,10 +874,15 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 const float sr = sqrtf(s_mx[par] / nr), fr = sqrtf(s_mx[par + 1] / nr),
                             gr = sqrtf(s_mx[par + 2] / nr), sc = sqrtf(s_mx[par + 4] / nc),
                             fc = sqrtf(s_mx[par + 5] / nc), gc = sqrtf(s_mx[par + 6] / nc);
-                if (threadIdx.x < 8) s_mx[8 - par + threadIdx.x] = 0.0f;  // the next chunk's set
+                const float hsum = RAW ? s_mx[par + 8] + s_mx[par + 9] : 0.0f;
+                if (threadIdx.x < 12) s_mx[12 - par + threadIdx.x] = 0.0f;  // the next chunk's set
                 e_c = fmaxf(e_c, sr * sc + 2.0f * (fr * gc + fc * gr));
                 e_steps += nrr;
-                const float e = kBiasSigma * (float)Tr::kEps * e_c * sqrtf((float)(e_steps + 16));
+                // RAW adds a bound on this chunk's FP32 rounding of h_i, h_j and of
+                // the score's two subtractions: about 3 eps (h_i + h_j) / 2 at most,
+                // covered by 2 kBiasSigma eps (largest h of the rows + of the columns)
+                const float e = kBiasSigma * (float)Tr::kEps *
+                                (e_c * sqrtf((float)(e_steps + 16)) + 2.0f * hsum);
                 const T inc = (T)(e - e_applied);
                 e_applied = e;
 #pragma unroll
@@ -862,15 +894,15 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
             // the recorded groups are replayed after the sub-chunk
             for (int s0 = 0; s0 < nrr; s0 += kQueue * D) {
                 const int s1 = min(nrr, s0 + kQueue * D);
-                const int qn = fast_subchunk<Tr, D, RC>(c, s0, s1, lane_off, q_c0, q_s);
+                const int qn = fast_subchunk<Tr, D, RC, RAW>(c, s0, s1, lane_off, q_c0, q_s);
                 for (int e = 0; e < qn; ++e) {
                     // replay a recorded group from its starting covariances, with
                     // bookkeeping (out of line: it is rare)
                     if constexpr (Tr::kBias)
-                        replay_group_f32<D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
+                        replay_group_f32<D, RAW>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
                                             q_s[e], kl, lane_off, lane, e_applied, sItems);
                     else
-                        replay_group<Tr, D>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
+                        replay_group<Tr, D, RAW>(P, sRow, sCol, rS, cS, rKey, cKey, hdr, q_c0[e], r,
                                             q_s[e], kl, lane_off, lane);
                 }
             }

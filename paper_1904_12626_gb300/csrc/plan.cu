@@ -189,6 +189,7 @@ __device__ __forceinline__ long long first_diag(int m, double ez, unsigned flags
 __global__ void family_descs_kernel(FamilyParams F)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int RAW = (F.flags & MP_FLAG_RAW) ? 1 : 0;
     const size_t ksz = sizeof(Key128);
     if (F.kind == 0 || F.kind == 2) {          // self-join / pan: one set, problem, output per m
         const int nset = F.kind == 0 ? 1 : F.nm;
@@ -199,7 +200,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         StatSet S;
         S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.partner = k;
         S.kmin = first_diag(m, F.ez, F.flags);
-        S.dir = 0; S.pad = 0;
+        S.dir = 0; S.raw = RAW;
         F.sets[k] = S;
         Prob P;
         P.rS32 = P.cS32 = F.s32 ? F.s32 + sb : nullptr;
@@ -213,7 +214,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         P.kmin = first_diag(m, F.ez, F.flags);
         P.kmax = l - 1;
         P.m = m;
-        P.pad = 0;
+        P.raw = RAW;
         F.probs[k] = P;
         FinDesc D;
         D.key = P.rKey;
@@ -228,7 +229,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         D.pi = F.pi_a + (long long)k * F.out_stride;
         D.scale = (F.flags & MP_FLAG_PAN_NORMALIZE) && F.kind == 2 ? 1.0 / sqrt(2.0 * m) : 1.0;
         D.m = m;
-        D.dir = 0;
+        D.dir = 0; D.raw = RAW; D.pad = 0;
         F.fins[k] = D;
         return;
     }
@@ -246,7 +247,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         StatSet S;
         S.x = F.x64; S.n = F.n; S.l = l; S.sbase = sb; S.m = m; S.partner = 1 - k;
         S.kmin = E;
-        S.dir = k == 0 ? 1 : -1; S.pad = 0;
+        S.dir = k == 0 ? 1 : -1; S.raw = RAW;
         F.sets[k] = S;
         if (k == 0) {
             Prob P;
@@ -266,7 +267,7 @@ __global__ void family_descs_kernel(FamilyParams F)
             P.kmin = E;
             P.kmax = l - 1;
             P.m = m;
-            P.pad = 0;
+            P.raw = RAW;
             F.probs[0] = P;
         }
         FinDesc D;
@@ -285,7 +286,7 @@ __global__ void family_descs_kernel(FamilyParams F)
         D.pi = k == 0 ? F.pi_a : F.pi_b;
         D.scale = 1.0;
         D.m = m;
-        D.dir = S.dir;
+        D.dir = S.dir; D.raw = RAW; D.pad = 0;
         F.fins[k] = D;
         return;
     }
@@ -297,7 +298,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     const long long sbA = 0, sbB = F.na + kPad;
     const double *xa = F.x64, *xb = F.x64 + F.na;
     StatSet S;
-    S.m = m; S.partner = 1 - k; S.kmin = -1; S.dir = 0; S.pad = 0;
+    S.m = m; S.partner = 1 - k; S.kmin = -1; S.dir = 0; S.raw = RAW;
     if (k == 0) { S.x = xa; S.n = F.na; S.l = la; S.sbase = sbA; }
     else { S.x = xb; S.n = F.nb; S.l = lb; S.sbase = sbB; }
     F.sets[k] = S;
@@ -322,7 +323,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     P.kmin = rowA ? 0 : 1;
     P.kmax = P.lC - 1;
     P.m = m;
-    P.pad = 0;
+    P.raw = RAW;
     F.probs[k] = P;
     FinDesc D;
     D.key = P.rKey;
@@ -335,7 +336,7 @@ __global__ void family_descs_kernel(FamilyParams F)
     D.pi = rowA ? F.pi_a : F.pi_b;
     D.scale = 1.0;
     D.m = m;
-    D.dir = 0;
+    D.dir = 0; D.raw = RAW; D.pad = 0;
     F.fins[k] = D;
 }
 
@@ -347,6 +348,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
                                      int64_t *pi, const int64_t *__restrict__ out_offsets,
                                      StatSet *sets, Prob *probs, FinDesc *fins, Hdr *hdr)
 {
+    const int RAW = (flags & MP_FLAG_RAW) ? 1 : 0;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const size_t ksz = sizeof(Key128);
@@ -369,7 +371,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     StatSet S;
     S.x = x64 + off; S.n = n; S.l = l; S.sbase = sb; S.m = m; S.partner = b;
     S.kmin = first_diag(m, ez, flags);
-    S.dir = 0; S.pad = 0;
+    S.dir = 0; S.raw = RAW;
     sets[b] = S;
     Prob P;
     P.rS32 = P.cS32 = s32 ? s32 + sb : nullptr;
@@ -383,7 +385,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     P.kmin = first_diag(m, ez, flags);
     P.kmax = l - 1;
     P.m = m;
-    P.pad = 0;
+    P.raw = RAW;
     probs[b] = P;
     FinDesc D;
     D.key = P.rKey;
@@ -398,7 +400,7 @@ __global__ void batched_descs_kernel(const int64_t *__restrict__ offsets,
     D.pi = (long long *)pi + out_offsets[b];
     D.scale = 1.0;
     D.m = m;
-    D.dir = 0;
+    D.dir = 0; D.raw = RAW; D.pad = 0;
     fins[b] = D;
 }
 

@@ -71,7 +71,9 @@ __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__re
         for (int k = 0; k < 2; ++k) {
             const long long j = k == 0 ? j1 : j2;
             if (j < 0 || (k == 1 && j == j1)) continue;
-            const double r = seed_dot(xw, muw, Y.x + j, S.m) * invw * inv[Y.sbase + j];
+            const double dot = seed_dot(xw, muw, Y.x + j, S.m);
+            // correlation, or the non-normalised score q - h_i - h_j (mu = 0, inv = h)
+            const double r = S.raw ? (dot - invw) - inv[Y.sbase + j] : dot * invw * inv[Y.sbase + j];
             if (FP64) {
                 if (best < 0 || r > rb) { best = j; rb = r; }
             } else {

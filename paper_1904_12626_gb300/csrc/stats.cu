@@ -76,6 +76,8 @@ __device__ __forceinline__ dd dd_div(dd a, double b)
 
 struct WindowOut {
     double mu, invn, df, dg;
+    double h;                                // ||x_i||^2 / 2 (non-normalised distance)
+    double dgr;                              // x_{i+m-1} + x_{i-1} (non-normalised recurrence)
     bool flat;
 };
 
@@ -112,14 +114,17 @@ __device__ __forceinline__ void walk_windows(const T *__restrict__ x, int m, lon
             o.mu = mu;
             o.flat = (changes == 0);
             o.invn = (o.flat || !(var.hi > 0.0)) ? 0.0 : 1.0 / sqrt(var.hi);
+            o.h = 0.5 * (s2.hi + s2.lo);
             if (w > 0) {
                 const double a = (double)x[w + m - 1];
                 const double b = (double)x[w - 1];
                 o.df = 0.5 * (a - b);
                 o.dg = (a - mu) + (b - mu_prev);
+                o.dgr = a + b;
             } else {
                 o.df = 0.0;
                 o.dg = 0.0;
+                o.dgr = 0.0;
             }
             emit(w, o);
         }
@@ -173,11 +178,21 @@ __global__ void stats_sets_kernel(const StatSet *__restrict__ sets, int nsets, l
             const long long base = S.sbase;
             double logsum = 0.0, cnt = 0.0;
             walk_windows<double>(S.x, S.m, i, vend, [&](long long w, const WindowOut &o) {
+                const long long q = base + w;
+                if (S.raw) {                            // non-normalised: q-recurrence terms
+                    const float ninf = __int_as_float(0xff800000);
+                    if (mu) mu[q] = 0.0;
+                    if (inv) inv[q] = o.h;
+                    if (flat) flat[q] = 0;
+                    if (s32) s32[q] = make_float4((float)o.df, (float)o.dgr, (float)o.h, ninf);
+                    if (s64) s64[q] = make_d4(o.df, o.dgr, o.h,
+                                              __longlong_as_double((long long)0xfff0000000000000ull));
+                    return;
+                }
                 if (o.invn > 0.0) {                     // norm statistics of the set
                     logsum -= log(o.invn);
                     cnt += 1.0;
                 }
-                const long long q = base + w;
                 if (mu) mu[q] = o.mu;
                 if (inv) inv[q] = o.invn;
                 if (flat) flat[q] = o.flat ? 1 : 0;

@@ -133,3 +133,19 @@ def sample_rows(l: int, count: int, seed: int) -> np.ndarray:
         return np.arange(l, dtype=np.int64)
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(l, size=count, replace=False)).astype(np.int64)
+
+
+def tonal(n: int, seed: int = 0, dtype=np.float64, n_tones: int = 4) -> np.ndarray:
+    """A bounded, music-like signal for the non-normalised distance (SiMPle's
+    domain, Sec. 3.3.4): a few sinusoids whose amplitudes drift slowly, plus
+    N(0, 0.05^2) noise; values stay within a few units of zero."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(n, dtype=np.float64)
+    x = np.zeros(n)
+    for _ in range(n_tones):
+        period = rng.uniform(12.0, 200.0)
+        phase = rng.uniform(0.0, 2.0 * np.pi)
+        amp = 0.5 + 0.5 * np.sin(2.0 * np.pi * t / rng.uniform(5000.0, 50000.0) + rng.uniform(0, 6.3))
+        x += amp * np.sin(2.0 * np.pi * t / period + phase)
+    x += 0.05 * rng.standard_normal(n)
+    return x.astype(dtype)

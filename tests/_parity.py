@@ -15,9 +15,16 @@ import oracle
 GAP = 1e-3
 
 
+def _raw_distance(x, y, m, i, j):
+    """||x_i - y_j||: the non-normalised distance, straight from its definition"""
+    return float(np.sqrt(np.sum((np.asarray(x[i:i + m], np.float64) -
+                                 np.asarray(y[j:j + m], np.float64)) ** 2)))
+
+
 def check_rows(x, m, rows, mp_gpu, pi_gpu, mp_or, pi_or, sec_or, tol, excl=None, inclusive=False,
-               y=None, gap=GAP):
-    """x: series (row side); y: candidate series for an AB-join (None: self)."""
+               y=None, gap=GAP, raw=False):
+    """x: series (row side); y: candidate series for an AB-join (None: self);
+    raw: the non-normalised distance."""
     rows = np.asarray(rows)
     mp_g = np.asarray(mp_gpu)[rows]
     pi_g = np.asarray(pi_gpu)[rows]
@@ -39,8 +46,8 @@ def check_rows(x, m, rows, mp_gpu, pi_gpu, mp_or, pi_or, sec_or, tol, excl=None,
         i, j = int(rows[r]), int(pi_g[r])
         if y is None:
             assert abs(i - j) >= (excl + 1 if inclusive else excl)
-            d = oracle.distance(x, m, i, j)
+            d = _raw_distance(x, x, m, i, j) if raw else oracle.distance(x, m, i, j)
         else:
-            d = oracle.distance_ab(x, y, m, i, j)
+            d = _raw_distance(x, y, m, i, j) if raw else oracle.distance_ab(x, y, m, i, j)
         assert abs(d - mp_or[r]) <= tol, f"row {i}: neighbour {j} at {d} vs best {mp_or[r]}"
     return float(np.max(np.abs(mp_g[fin] - mp_or[fin]))) if fin.any() else 0.0

@@ -37,6 +37,7 @@ MUTANTS = {
                   "double iac = 1.0 * (double)k * (double)(l - k) / (double)l;"),
     "diag_mask_signed": ("if (J->diag_ok && !J->diag_ok[d]) return 0;",
                          "if (J->diag_ok && !J->diag_ok[j > i ? j - i : 0]) return 0;"),
+    "raw_unsquared": ("                    acc += e * e;", "                    acc += fabs(e);"),
     "lr_sides_swapped": ("if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;",
                          "if ((J->side > 0 && j >= i) || (J->side < 0 && j <= i)) return 0;"),
 }

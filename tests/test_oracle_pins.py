@@ -233,6 +233,35 @@ def test_selfjoin_diags_against_scipy_and_special_cases():
         assert mp1[i] == min(ds) and pi1[i] == cands[int(np.argmin(ds))]
 
 
+@pytest.mark.parametrize("inclusive", [False, True])
+def test_raw_join_against_scipy(inclusive):
+    """Non-normalised distance (SiMPle, Sec. 3.3.4): scipy's Euclidean
+    distance matrix of the raw windows; shift and scale behave as the
+    definition says; flat windows get no special rule."""
+    rng = np.random.default_rng(19)
+    x = np.cumsum(rng.standard_normal(240))
+    x[60:90] = x[59]                          # flat windows are ordinary here
+    m = 10
+    E = oracle.exclusion_zone(m)
+    W = sliding_window_view(x, m)
+    D = scipy_dist.cdist(W, W, "euclidean")
+    ii, jj = np.indices(D.shape)
+    D[(np.abs(ii - jj) <= E) if inclusive else (np.abs(ii - jj) < E)] = np.inf
+    mp, pi, _ = oracle.join_raw(x, m, inclusive=inclusive)
+    np.testing.assert_allclose(mp, D.min(axis=1), atol=1e-10)
+    srt = np.sort(D, axis=1)
+    sep = srt[:, 1] - srt[:, 0] > 1e-9
+    np.testing.assert_array_equal(pi[sep], D.argmin(axis=1)[sep])
+    mp2, pi2, _ = oracle.join_raw(3.0 * x - 11.0, m, inclusive=inclusive)
+    np.testing.assert_allclose(mp2, 3.0 * mp, rtol=1e-9)
+    np.testing.assert_array_equal(pi2[sep], pi[sep])
+    b = rng.standard_normal(150)
+    mpab, piab, _ = oracle.join_raw(x, m, b=b)
+    Dab = scipy_dist.cdist(W, sliding_window_view(b, m), "euclidean")
+    np.testing.assert_allclose(mpab, Dab.min(axis=1), atol=1e-10)
+    np.testing.assert_array_equal(piab, Dab.argmin(axis=1))
+
+
 def test_abjoin_against_scipy_bruteforce():
     a = synth.random_walk(180, seed=7)
     b, _ = synth.mixed_with_flats(260, 8, seed=9, block=32, n_flat=2, flat_len=16)
