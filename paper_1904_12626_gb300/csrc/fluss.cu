@@ -198,18 +198,44 @@ __global__ void __launch_bounds__(kSegThreads) seg_partial_kernel(const double *
     }
 }
 
-// pass 2: the minimum over the blocks is boundary s
-__global__ void seg_pick_kernel(const double *pv, const long long *pidx, int nblocks,
-                                int64_t *segments, int s)
+// pass 2: the minimum over the blocks' minima is boundary s (one block)
+__global__ void __launch_bounds__(kSegThreads) seg_pick_kernel(const double *pv,
+                                                               const long long *pidx,
+                                                               int nblocks, int64_t *segments,
+                                                               int s)
 {
+    __shared__ double s_v[kSegThreads / 32];
+    __shared__ long long s_i[kSegThreads / 32];
     double bv = INFINITY;
     long long bi = -1;
-    for (int b = 0; b < nblocks; ++b)
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
         if (seg_better(pv[b], pidx[b], bv, bi)) {
             bv = pv[b];
             bi = pidx[b];
         }
-    segments[s] = bi;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (seg_better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        s_v[warp] = bv;
+        s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kSegThreads / 32; ++w)
+            if (seg_better(s_v[w], s_i[w], bv, bi)) {
+                bv = s_v[w];
+                bi = s_i[w];
+            }
+        segments[s] = bi;
+    }
 }
 
 }  // namespace
@@ -253,7 +279,7 @@ cudaError_t launch_fluss(const int64_t *pi, long long l, long long edge, int num
         for (int sg = 0; sg < num_segments; ++sg) {
             seg_partial_kernel<<<(unsigned)nblk, kSegThreads, 0, st>>>(cac, l, segments, sg,
                                                                      seg_excl, pv, pidx);
-            seg_pick_kernel<<<1, 1, 0, st>>>(pv, pidx, (int)nblk, segments, sg);
+            seg_pick_kernel<<<1, kSegThreads, 0, st>>>(pv, pidx, (int)nblk, segments, sg);
         }
     }
     return cudaGetLastError();

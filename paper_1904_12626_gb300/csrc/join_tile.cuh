@@ -654,7 +654,7 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
 }
 
 // groups the fast path records before their replays run
-constexpr int kQueue = 8;
+constexpr int kQueue = 16;
 
 // The hot loop: rows s0 .. s1-1 of the staged chunk (whole groups of D rows)
 // for this thread's D diagonals.  Each cell costs two FMAs (the covariance
