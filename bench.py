@@ -151,6 +151,12 @@ def max_over_ranks(v: float, world: int) -> float:
     return float(t.item())
 
 
+def replica_value(world: int, cells: int, steps: int, total_ms: float) -> float:
+    """Whole-job Gcells/s: every rank joins its own copy of the workload (the
+    self-join needs no exchange), timed by the slowest rank."""
+    return world * cells * steps / (total_ms / 1e3) / 1e9
+
+
 def workload(n: int, m: int):
     from paper_1904_12626_gb300 import synth
     x, info = synth.planted_walk(n, m, seed=SEED)
@@ -325,7 +331,7 @@ def run_ours(args, world, rank, local):
     kernel_ms = max_over_ranks(statistics.mean(kern_ms), world)
     if anytime:                # the tile kernel runs twice per step: judge the whole step
         kernel_ms = total_ms / args.steps
-    value = world * cells * args.steps / (total_ms / 1e3) / 1e9
+    value = replica_value(world, cells, args.steps, total_ms)
 
     # all-FP64 kernel on the same input (comparison leg, one warm-up + timed steps)
     fp64 = None
@@ -507,8 +513,9 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
     ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss"), default="self")
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--m", type=int, default=M_DEFAULT)
+    # long aliases: under torchrun, --n / --m prefix-match the launcher's own options
+    ap.add_argument("--n", "--series-length", dest="n", type=int, default=N_DEFAULT)
+    ap.add_argument("--m", "--window", dest="m", type=int, default=M_DEFAULT)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
