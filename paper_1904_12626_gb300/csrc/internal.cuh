@@ -106,7 +106,7 @@ struct Prob {
 
 struct Band {
     int prob;
-    int pad;
+    int tile_rows;                        // rows per tile of this band
     long long k0;                         // first diagonal of the band
 };
 

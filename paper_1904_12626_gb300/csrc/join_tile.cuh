@@ -754,6 +754,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     // size the error bias
     __shared__ float s_mx[24];
 
+    (void)tile_rows;                           // each band carries its own tile height
     const int lane = threadIdx.x & 31;
     const int lane_off = threadIdx.x * D;
     const int nb = hdr->nbands;
@@ -779,8 +780,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
         const long long k0 = bd.k0;
         const long long lR = P.lR, lC = P.lC;
         const long long rows_end = min(lR, lC - k0);
-        const long long i0 = (long long)(tile - tile_prefix[lo]) * tile_rows;
-        const long long i1 = min(i0 + (long long)tile_rows, rows_end);
+        const long long i0 = (long long)(tile - tile_prefix[lo]) * bd.tile_rows;
+        const long long i1 = min(i0 + (long long)bd.tile_rows, rows_end);
         const long long kl = k0 + lane_off;        // slot d walks diagonal kl + d
         S4 *rS = Tr::rs(P);
         S4 *cS = Tr::cs(P);

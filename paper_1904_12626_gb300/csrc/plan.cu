@@ -55,6 +55,9 @@ __device__ void block_exclusive_scan(T *a, long long n)
     __syncthreads();
 }
 
+constexpr int kEarlyBands = 16;            // bands of each problem planned in short tiles
+constexpr int kEarlyTileRows = 1024;
+
 __global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, int TR,
                             long long *band_off, Band *bands, unsigned long long *tile_prefix,
                             long long max_bands, Hdr *hdr)
@@ -79,12 +82,17 @@ __global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, i
             for (long long b = 0; b < nb; ++b) {
                 const long long k0 = P.kmin + b * TD;
                 const long long rows = min(P.lR, P.lC - k0);
+                // the first bands go in short tiles: with tiles of TR rows about
+                // (CTAs / tiles per band) bands would run at once, all against the
+                // seeds' thresholds; short tiles let them finish nearly in order,
+                // so each starts from the keys its predecessors improved
+                const int tr = b < kEarlyBands ? (TR < kEarlyTileRows ? TR : kEarlyTileRows) : TR;
                 Band bd;
                 bd.prob = p;
-                bd.pad = 0;
+                bd.tile_rows = tr;
                 bd.k0 = k0;
                 bands[off + b] = bd;
-                tile_prefix[off + b] = rows > 0 ? (unsigned long long)((rows + TR - 1) / TR) : 0ull;
+                tile_prefix[off + b] = rows > 0 ? (unsigned long long)((rows + tr - 1) / tr) : 0ull;
             }
         }
     }
