@@ -299,9 +299,12 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     api.device_status(ws)
 
-    # convert, descriptors, stats, fragile marking, key seeding, plan, tile kernel,
-    # fragile pass, finalize
-    launches_per_step = 17 if anytime else 9      # anytime: begin (7) + two runs (5 each)
+    # convert, descriptors, stats, fragile marking, key seeding (FP32: three kernels,
+    # FP64: one), plan, tile kernel, fragile pass, finalize; anytime: begin (the same up
+    # to the plan, plus the band order) and two runs (bind, window, tile kernel,
+    # fragile pass, finalize)
+    seed_launches = 3 if args.prec == "fp32" else 1
+    launches_per_step = (7 + seed_launches + 10) if anytime else (8 + seed_launches)
     td, rc = ctypes.c_int32(), ctypes.c_int32()
     prec_id = 1 if args.prec == "fp32" else 0
     _lib.check(lib.mp_variant_info(prec_id, cfg.variant, ctypes.byref(td), ctypes.byref(rc)),

@@ -42,11 +42,11 @@ __device__ __forceinline__ double seed_dot(const double *__restrict__ xa, double
 template <bool FP64>
 __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__restrict__ mu,
                             const double *__restrict__ inv, const uint8_t *__restrict__ flat,
-                            float4 *s32, D4 *s64, Key128 *keys)
+                            float4 *s32, D4 *s64, Key128 *keys, int skip_self)
 {
     const int set = blockIdx.y;
     const StatSet S = sets[set];
-    if (S.l <= 0) return;
+    if (S.l <= 0 || (skip_self && S.kmin >= 0)) return;
     const StatSet Y = sets[S.partner];
     if (Y.l <= 0) return;
     for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < S.l;
@@ -95,6 +95,83 @@ __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__re
     }
 }
 
+// ---- FP32 path, self-join sets: the same seeds by the diagonal recurrence ----
+//
+// The pairs (w, w + kmin) all lie on diagonal kmin, so instead of two dot
+// products per window a thread walks kSeedRun windows of that diagonal: an
+// exact FP64 dot product at the run's start, then the FP64 recurrence
+// c += df_w dg_j + df_j dg_w.  Window w offers j = w + kmin to its own key (its
+// right side) and j receives w (its left side); a key takes the larger value,
+// the lower index on a tie, through an integer max on the FP32 keys' high word
+// (value, inverted index).  seed_finish_kernel completes the keys (exact: the
+// lower bound is the value) and the thresholds.
+constexpr int kSeedRun = 128;
+
+__device__ __forceinline__ unsigned long long seed_pack(double r, long long idx)
+{
+    const float v = (float)r + 0.0f;
+    return ((unsigned long long)ord32(__float_as_uint(v)) << 32) |
+           (unsigned long long)(0xFFFFFFFFu - (unsigned)idx);
+}
+
+__global__ void seed_diag_kernel(const StatSet *__restrict__ sets, const double *__restrict__ mu,
+                                 const double *__restrict__ inv, const uint8_t *__restrict__ flat,
+                                 const D4 *__restrict__ s64, Key128 *keys)
+{
+    const StatSet S = sets[blockIdx.y];
+    if (S.l <= 0 || S.kmin < 0 || S.dir < 0) return;     // AB sets; left roles are filled here
+    const StatSet Y = sets[S.partner];
+    const long long k = S.kmin;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kSeedRun;
+    long long wend = w0 + kSeedRun;
+    if (wend > S.l) wend = S.l;
+    if (wend > Y.l - k) wend = Y.l - k;                  // j = w + k must be a window
+    if (w0 >= wend) return;
+    const double *ir = inv + S.sbase, *ic = inv + Y.sbase;
+    const D4 *sr = s64 + S.sbase, *sc = s64 + Y.sbase;
+    const uint8_t *fr = flat + S.sbase, *fc = flat + Y.sbase;
+    const double *xa = S.x + w0, *xb = Y.x + w0 + k;
+    const double ma = mu[S.sbase + w0];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int t = 0;
+    for (; t + 3 < S.m; t += 4) {
+        a0 = fma(xa[t] - ma, xb[t], a0);
+        a1 = fma(xa[t + 1] - ma, xb[t + 1], a1);
+        a2 = fma(xa[t + 2] - ma, xb[t + 2], a2);
+        a3 = fma(xa[t + 3] - ma, xb[t + 3], a3);
+    }
+    for (; t < S.m; ++t) a0 = fma(xa[t] - ma, xb[t], a0);
+    double c = (a0 + a1) + (a2 + a3);
+    Key128 *kr = keys + S.sbase, *kc = keys + Y.sbase;
+    for (long long w = w0; w < wend; ++w) {
+        const long long j = w + k;
+        const double r = S.raw ? (c - ir[w]) - ic[j] : c * ir[w] * ic[j];
+        if (!fr[w]) atomicMax(&kr[w].hi, seed_pack(r, j));
+        if (!fc[j]) atomicMax(&kc[j].hi, seed_pack(r, w));
+        if (w + 1 < wend) {
+            const D4 a = sr[w + 1], b = sc[j + 1];
+            c = fma(a.x, b.y, c);
+            c = fma(b.x, a.y, c);
+        }
+    }
+}
+
+// complete the seeded keys (exact: lower bound = value) and their thresholds
+__global__ void seed_finish_kernel(const StatSet *__restrict__ sets,
+                                   const uint8_t *__restrict__ flat, float4 *s32, Key128 *keys)
+{
+    const StatSet S = sets[blockIdx.y];
+    if (S.l <= 0 || S.kmin < 0) return;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < S.l;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long q = S.sbase + w;
+        const unsigned long long hi = keys[q].hi;
+        if (hi == 0ull || flat[q]) continue;
+        keys[q].lo = hi & 0xFFFFFFFF00000000ull;
+        s32[q].w = __uint_as_float(unord32((unsigned)(hi >> 32)));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_seed(const StatSet *sets, int nsets, long long max_l, const double *mu,
@@ -107,12 +184,17 @@ cudaError_t launch_seed(const StatSet *sets, int nsets, long long max_l, const d
     const long long cap = 65536 / nsets > 0 ? 65536 / nsets : 1;
     if (per > cap) per = cap;
     const dim3 grid((unsigned)per, (unsigned)nsets);
-    if (fp64)
-        seed_kernel<true><<<grid, threads, 0, st>>>(sets, mu, inv, flat, s32, s64,
-                                                     reinterpret_cast<Key128 *>(keys));
-    else
-        seed_kernel<false><<<grid, threads, 0, st>>>(sets, mu, inv, flat, s32, s64,
-                                                      reinterpret_cast<Key128 *>(keys));
+    Key128 *k128 = reinterpret_cast<Key128 *>(keys);
+    if (fp64) {
+        seed_kernel<true><<<grid, threads, 0, st>>>(sets, mu, inv, flat, s32, s64, k128, 0);
+        return cudaGetLastError();
+    }
+    // FP32 path: AB sets from a dot product each, self-join sets along diagonal kmin
+    seed_kernel<false><<<grid, threads, 0, st>>>(sets, mu, inv, flat, s32, s64, k128, 1);
+    const long long runs = (max_l + kSeedRun - 1) / kSeedRun;
+    const dim3 gd((unsigned)((runs + 127) / 128), (unsigned)nsets);
+    seed_diag_kernel<<<gd, 128, 0, st>>>(sets, mu, inv, flat, s64, k128);
+    seed_finish_kernel<<<grid, threads, 0, st>>>(sets, flat, s32, k128);
     return cudaGetLastError();
 }
 
