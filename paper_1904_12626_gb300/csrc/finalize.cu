@@ -26,6 +26,30 @@ __device__ __forceinline__ double exact_distance(const FinDesc &F, long long i, 
     const double invC = F.invC[j];
     const double muR = F.muR[i], muC = F.muC[j];
     const double *xr = F.xR + i, *xc = F.xC + j;
+    // Through the correlation first: d^2 = 2m(1 - rho), three FP64 operations per
+    // sample (both windows centred: leaving the column's mean out, exact in exact
+    // arithmetic, lets the rounding of the row's mean meet the column's offset,
+    // which ill-conditioned windows would notice).  The rounding of rho (a few
+    // ulps, times 2m) only matters when d is small, so below d^2 = 1 the distance
+    // is summed directly from its definition.
+    {
+        double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+        int t = 0;
+        for (; t + 3 < F.m; t += 4) {
+            c0 = fma(xr[t] - muR, xc[t] - muC, c0);
+            c1 = fma(xr[t + 1] - muR, xc[t + 1] - muC, c1);
+            c2 = fma(xr[t + 2] - muR, xc[t + 2] - muC, c2);
+            c3 = fma(xr[t + 3] - muR, xc[t + 3] - muC, c3);
+        }
+        for (; t < F.m; ++t) c0 = fma(xr[t] - muR, xc[t] - muC, c0);
+        const double rho = ((c0 + c1) + (c2 + c3)) * invR * invC;
+        const double d2 = 2.0 * (double)F.m * (1.0 - rho);
+        if (d2 >= 1.0) {
+            const double d = sqrt(d2);
+            const double cap = 2.0 * sqrt((double)F.m);
+            return d > cap ? cap : d;
+        }
+    }
     double a0 = 0.0, a1 = 0.0;                    // two chains: FP64 latency
     int t = 0;
     for (; t + 1 < F.m; t += 2) {
