@@ -484,10 +484,15 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
                 if (p > top) top = p;
             }
         }
+        // most replayed rows have no cell at the row's threshold: skip the reduction
+        if (!__any_sync(0xffffffffu, top != 0ull)) {
+            top = 0ull;
+        } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
-            if (y > top) top = y;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
+                if (y > top) top = y;
+            }
         }
         if (top != 0ull) {                      // warp-uniform
             const long long jt = TraitsF32::pidx(top);
