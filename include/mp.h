@@ -144,7 +144,7 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
                       double *mp, int64_t *pi, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * Left and right self-join profiles (used by time series chains, Sec. 3.4.4):
+ * Left and right self-join profiles (used by time series chains, Sec. 3.4.3):
  * for window i, mp_left[i] / pi_left[i] is its nearest neighbour among the
  * windows j before it (i - j >= E, E the exclusion zone of cfg), and
  * mp_right[i] / pi_right[i] among the windows after it (j - i >= E).  With
@@ -187,7 +187,7 @@ mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, doubl
                          int64_t *pi, void *ws, size_t ws_bytes, void *stream);
 
 /*
- * Semantic segmentation from a self-join profile index (FLUSS, Sec. 3.4.3).
+ * Semantic segmentation from a self-join profile index (FLUSS, Sec. 3.4.2).
  * pi: l int64 (device; entries < 0 mean "no neighbour"; entries >= l are
  * skipped and set MP_EINVAL in the workspace status, read it with
  * mp_get_device_status).  Every window i with pi[i] >= 0 is an arc between
@@ -198,7 +198,7 @@ mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, doubl
  *   segments (num_segments int64, device; may be NULL when num_segments = 0):
  *   the position of the lowest cac (lowest index on ties), then the lowest
  *   outside |k - s| < seg_excl of every earlier one; -1 once none is left.
- * The paper (Sec. 3.4.3) shows only the number of segments being chosen; both
+ * The paper (Sec. 3.4.2) shows only the number of segments being chosen; both
  * margins are left to the caller (the Python binding defaults both to 5m).
  * ws/ws_bytes: scratch of at least mp_fluss_workspace_bytes(l) bytes.
  */

@@ -324,7 +324,7 @@ int oracle_selfjoin(const double *x, int64_t n, int32_t m, int64_t excl, int inc
 /*
  * Left (side = -1) or right (side = +1) self-join profile: as oracle_selfjoin,
  * with the candidates restricted to the windows before (after) row i.  The
- * paper's time series chains (Sec. 3.4.4) are built on these two profiles; the
+ * paper's time series chains (Sec. 3.4.3) are built on these two profiles; the
  * paper gives no formula, so this is the self-join definition above with the
  * candidate set cut in two.
  */
@@ -406,7 +406,7 @@ int oracle_abjoin(const double *a, int64_t na, const double *b, int64_t nb, int3
 }
 
 /*
- * ---- semantic segmentation (Sec. 3.4.3, FLUSS after Gharghabi et al.) ----
+ * ---- semantic segmentation (Sec. 3.4.2, FLUSS after Gharghabi et al.) ----
  *
  * The paper cites the method without formulas; these follow its published
  * description.  Each window i with a neighbour pi[i] >= 0 is an arc between

@@ -1,5 +1,5 @@
 // fluss.cu -- semantic segmentation from a profile index (FLUSS, the paper's
-// Sec. 3.4.3 "Semantic segmentation", after Gharghabi et al. 2017).
+// Sec. 3.4.2 "Semantic segmentation", after Gharghabi et al. 2017).
 //
 // Every window i with a neighbour PI[i] >= 0 draws an arc between i and
 // PI[i].  A regime change is a place few arcs cross: windows of one regime

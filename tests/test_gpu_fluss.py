@@ -1,4 +1,4 @@
-"""GPU parity of semantic segmentation (FLUSS, Sec. 3.4.3) through the C ABI
+"""GPU parity of semantic segmentation (FLUSS, Sec. 3.4.2) through the C ABI
 against the oracle: the arc counts are integers, so the corrected arc curve
 (the same double expression on both sides) and the boundaries must match
 exactly."""

@@ -1,5 +1,5 @@
 """GPU parity of the left / right self-join profiles (the profiles time series
-chains are built on, Sec. 3.4.4): CUDA path through the C ABI vs the oracle."""
+chains are built on, Sec. 3.4.3): CUDA path through the C ABI vs the oracle."""
 import math
 
 import numpy as np

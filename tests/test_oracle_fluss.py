@@ -1,4 +1,4 @@
-"""Pins of the oracle's semantic segmentation (FLUSS, Sec. 3.4.3): a worked
+"""Pins of the oracle's semantic segmentation (FLUSS, Sec. 3.4.2): a worked
 example by hand, the O(l) arc count against the definition, the expected
 arc count of random neighbours, and a regime change found by the oracle's own
 self-join."""

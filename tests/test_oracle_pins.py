@@ -176,7 +176,7 @@ def test_selfjoin_against_scipy_bruteforce(n, m, ez, inclusive, seed):
 @pytest.mark.parametrize("n,m,ez,inclusive,seed", [
     (64, 8, 0.5, False, 11), (120, 8, 0.25, True, 12), (301, 16, 0.5, False, 13)])
 def test_selfjoin_lr_against_scipy_bruteforce(n, m, ez, inclusive, seed):
-    """Left / right profiles (the basis of time series chains, Sec. 3.4.4):
+    """Left / right profiles (the basis of time series chains, Sec. 3.4.3):
     the self-join definition with the candidates cut at the row."""
     x = synth.random_walk(n, seed=seed)
     if seed == 13:
