@@ -106,3 +106,31 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.mp_get_device_status(None, None) == E
     for code in range(7):
         assert lib.mp_status_string(code).decode()
+
+
+def test_host_checks_of_the_newer_entry_points(lib):
+    """Left/right, anytime, FLUSS and the non-normalised flag: invalid calls
+    are rejected on the host, workspace queries answer without a GPU."""
+    cfg = _lib.make_config(64)
+    fake = 256 * 1024
+    E = _lib.MP_EINVAL
+    assert lib.mp_selfjoin_lr_workspace_bytes(4096, ctypes.byref(cfg)) > \
+        lib.mp_selfjoin_workspace_bytes(4096, ctypes.byref(cfg))
+    assert lib.mp_selfjoin_lr(fake, 0, 4096, ctypes.byref(cfg), fake, None, fake, fake, fake,
+                              1 << 30, None) == E
+    assert lib.mp_selfjoin_lr(fake, 0, 4096, ctypes.byref(cfg), fake, fake, fake, fake, fake + 8,
+                              1 << 30, None) == E
+    assert lib.mp_anytime_workspace_bytes(4096, ctypes.byref(cfg)) == \
+        lib.mp_selfjoin_workspace_bytes(4096, ctypes.byref(cfg))
+    assert lib.mp_anytime_begin(None, 0, 4096, ctypes.byref(cfg), 1, fake, 1 << 30, None) == E
+    for f in (-0.1, 1.5, float("nan")):
+        assert lib.mp_anytime_run(4096, ctypes.byref(cfg), f, fake, fake, fake, 1 << 30, None) == E
+    assert lib.mp_fluss_workspace_bytes(0) == 0 and lib.mp_fluss_workspace_bytes(1 << 20) > 0
+    assert lib.mp_fluss(None, 100, 0, 1, 0, fake, fake, fake, 1 << 20, None) == E
+    assert lib.mp_fluss(fake, 100, -1, 1, 0, fake, fake, fake, 1 << 20, None) == E
+    assert lib.mp_fluss(fake, 100, 0, 2, 0, fake, None, fake, 1 << 20, None) == E
+    assert lib.mp_fluss(fake, 100, 0, 1, 0, fake, fake, fake, 16, None) == _lib.MP_ENOMEM
+    raw1 = _lib.make_config(64, flags=_lib.MP_FLAG_RAW, variant=1)
+    assert lib.mp_selfjoin_workspace_bytes(4096, ctypes.byref(raw1)) == 0   # default shape only
+    raw0 = _lib.make_config(64, flags=_lib.MP_FLAG_RAW)
+    assert lib.mp_selfjoin_workspace_bytes(4096, ctypes.byref(raw0)) > 0
