@@ -182,7 +182,7 @@ mp_status prepare_join(const Layout &L, const LayoutReq &r, const TileCfg &t, lo
     MP_CU(launch_seed(L.sets, r.nsets, max_fin_len, L.mu, L.inv, L.flat, L.s32, L.s64, L.keys,
                       t.fp64, st));
     MP_CU(launch_plan(L.probs, r.nprob, t.tile_diags, t.tile_rows, L.band_off, L.bands,
-                      L.tile_prefix, r.max_bands, L.hdr, st));
+                      L.tile_prefix, L.scratch, r.max_bands, L.hdr, st));
     return MP_OK;
 }
 

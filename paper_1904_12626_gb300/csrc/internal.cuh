@@ -219,9 +219,10 @@ cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, do
                                 cudaStream_t st);
 
 // plan.cu
+// scratch: at least max_bands + 1 long longs
 cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
                         long long *band_off, Band *bands, unsigned long long *tile_prefix,
-                        long long max_bands, Hdr *hdr, cudaStream_t st);
+                        long long *scratch, long long max_bands, Hdr *hdr, cudaStream_t st);
 // anytime self-join: put the bands in a seeded random order (splitmix64,
 // Fisher-Yates) and open the window of bands [done, ceil(fraction * total))
 cudaError_t launch_permute_bands(unsigned long long seed, Band *bands,

@@ -58,42 +58,69 @@ __device__ void block_exclusive_scan(T *a, long long n)
 constexpr int kEarlyBands = 16;            // bands of each problem planned in short tiles
 constexpr int kEarlyTileRows = 1024;
 
+// Band order: round b holds band b of every problem that has one, problems in
+// order.  The tile queue hands out tickets in this order, so the CTAs in flight
+// at any time work on neighbouring bands of many problems, and each problem's
+// bands start roughly nearest first: a band then compares against keys its
+// problem's earlier bands have already improved.  (In problem-major order all
+// the bands of a small problem would run at once against the seeds alone and
+// most of their candidates would lose at the keys.)
 __global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, int TR,
                             long long *band_off, Band *bands, unsigned long long *tile_prefix,
-                            long long max_bands, Hdr *hdr)
+                            long long max_bands, long long *scratch, Hdr *hdr)
 {
+    __shared__ long long s_max[32];
+    long long my_max = 0;
     for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
         const Prob P = probs[p];
         long long nb = 0;
         if (P.lR > 0 && P.lC > 0 && P.kmax >= P.kmin) nb = (P.kmax - P.kmin) / TD + 1;
         band_off[p] = nb;
+        my_max = nb > my_max ? nb : my_max;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long y = __shfl_xor_sync(0xffffffffu, my_max, o);
+        my_max = y > my_max ? y : my_max;
+    }
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = my_max;
     __syncthreads();
+    long long max_nb = 0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) max_nb = s_max[w] > max_nb ? s_max[w] : max_nb;
     block_exclusive_scan<long long>(band_off, nprob);
     long long total = band_off[nprob];
     if (total > max_bands) {                   // workspace sized too small: plan nothing
         if (threadIdx.x == 0) set_status(hdr, MP_ENOMEM);
         total = 0;
+        max_nb = 0;
     }
-    if (total > 0) {
-        for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+    // slots of round b start at the number of bands of the earlier rounds
+    for (long long b = threadIdx.x; b < max_nb; b += blockDim.x) {
+        long long c = 0;
+        for (int p = 0; p < nprob; ++p) c += (band_off[p + 1] - band_off[p]) > b;
+        scratch[b] = c;
+    }
+    __syncthreads();
+    block_exclusive_scan<long long>(scratch, max_nb);
+    for (long long b = threadIdx.x; b < max_nb; b += blockDim.x) {
+        long long slot = scratch[b];
+        // the first bands go in short tiles: with tiles of TR rows about
+        // (CTAs / tiles per band) bands would run at once, all against the
+        // seeds' thresholds; short tiles let them finish nearly in order,
+        // so each starts from the keys its predecessors improved
+        const int tr = b < kEarlyBands ? (TR < kEarlyTileRows ? TR : kEarlyTileRows) : TR;
+        for (int p = 0; p < nprob; ++p) {
+            if (band_off[p + 1] - band_off[p] <= b) continue;
             const Prob P = probs[p];
-            const long long off = band_off[p], nb = band_off[p + 1] - off;
-            for (long long b = 0; b < nb; ++b) {
-                const long long k0 = P.kmin + b * TD;
-                const long long rows = min(P.lR, P.lC - k0);
-                // the first bands go in short tiles: with tiles of TR rows about
-                // (CTAs / tiles per band) bands would run at once, all against the
-                // seeds' thresholds; short tiles let them finish nearly in order,
-                // so each starts from the keys its predecessors improved
-                const int tr = b < kEarlyBands ? (TR < kEarlyTileRows ? TR : kEarlyTileRows) : TR;
-                Band bd;
-                bd.prob = p;
-                bd.tile_rows = tr;
-                bd.k0 = k0;
-                bands[off + b] = bd;
-                tile_prefix[off + b] = rows > 0 ? (unsigned long long)((rows + tr - 1) / tr) : 0ull;
-            }
+            const long long k0 = P.kmin + b * TD;
+            const long long rows = min(P.lR, P.lC - k0);
+            Band bd;
+            bd.prob = p;
+            bd.tile_rows = tr;
+            bd.k0 = k0;
+            bands[slot] = bd;
+            tile_prefix[slot] = rows > 0 ? (unsigned long long)((rows + tr - 1) / tr) : 0ull;
+            ++slot;
         }
     }
     __syncthreads();
@@ -176,10 +203,11 @@ __global__ void anytime_window_kernel(double fraction, const unsigned long long 
 
 cudaError_t launch_plan(const Prob *probs, int nprob, int tile_diags, int tile_rows,
                         long long *band_off, Band *bands, unsigned long long *tile_prefix,
+                        long long *scratch,
                         long long max_bands, Hdr *hdr, cudaStream_t st)
 {
     plan_kernel<<<1, 1024, 0, st>>>(probs, nprob, tile_diags, tile_rows, band_off, bands,
-                                    tile_prefix, max_bands, hdr);
+                                    tile_prefix, max_bands, scratch, hdr);
     return cudaGetLastError();
 }
 
