@@ -513,6 +513,121 @@ def run_fluss(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_family(args, world, rank, local):
+    """--join ab | batched | pan: the other join families at their parity-test
+    sizes (AB: a 2^21 walk against a 2^19 walk / white-noise mix with flat
+    stretches, m = 512; batched: 4096 ragged walks of 1000..65536 samples,
+    m in {32, 64, 128}; pan: a 2^16 walk over 64 window sizes 16..1024),
+    FP32-mixed, L2 flushed between steps, timed like the self-join."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, build, synth
+    build.build()
+    api.init()
+    lib = _lib.load()
+    _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    if args.join == "ab":
+        m = 512
+        a_np = synth.random_walk(1 << 21, seed=51, dtype=np.float32)
+        b_np, _ = synth.mixed_with_flats(1 << 19, m, seed=52)
+        la, lb = len(a_np) - m + 1, len(b_np) - m + 1
+        cells = la * lb
+        inputs = [a_np, b_np]
+        desc = f"AB-join, 2^21 random walk x 2^19 walk/white-noise mix with flat stretches, m={m}"
+        def call(xs):
+            return api.abjoin(xs[0], xs[1], m, "fp32")
+        out_bytes = 16 * (la + lb)
+    elif args.join == "batched":
+        values, offsets, ms = synth.ragged_batch(4096, seed=55)
+        cells = 0
+        for b in range(len(ms)):
+            l_b = int(offsets[b + 1] - offsets[b]) - int(ms[b]) + 1
+            cells += selfjoin_cells(l_b, math.ceil(0.5 * int(ms[b])))
+        o_t = torch.from_numpy(offsets).cuda()
+        m_t = torch.from_numpy(ms).cuda()
+        inputs = [values]
+        max_m = int(ms.max())
+        desc = "batched self-joins, 4096 random walks of 1000..65536 samples, m in {32,64,128}"
+        def call(xs):
+            mp, pi, _ = api.batched(xs[0], o_t, m_t, max_m=max_m)
+            return mp, pi
+        out_bytes = 16 * len(values)
+    else:
+        n = 1 << 16
+        ms = synth.pan_windows()
+        x_np = synth.random_walk(n, seed=57, dtype=np.float32)
+        cells = sum(selfjoin_cells(n - int(mk) + 1, math.ceil(0.5 * int(mk))) for mk in ms)
+        inputs = [x_np]
+        desc = "pan profile, 2^16 random walk, 64 window sizes 16..1024"
+        def call(xs):
+            return api.pan(xs[0], ms)
+        out_bytes = 16 * len(ms) * (n - int(ms.min()) + 1)
+    dev_in = [torch.from_numpy(v).cuda() for v in inputs]
+    for _ in range(args.warmup):
+        call(dev_in)
+    torch.cuda.synchronize()
+    kms = ctypes.c_float()
+    times, kern = [], []
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            call(dev_in)
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+            _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+            kern.append(kms.value)
+    barrier(world)
+    total_ms = max_over_ranks(sum(times), world)
+    kernel_ms = max_over_ranks(statistics.mean(kern), world)
+    host_in = [torch.from_numpy(v).pin_memory() for v in inputs]
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        res = call([h.to("cuda", non_blocking=True) for h in host_in])
+        _ = [r.to("cpu", non_blocking=True) for r in res if r is not None]
+        e.record()
+        e.synchronize()
+        if it >= args.warmup:
+            e2e.append(s.elapsed_time(e))
+    e2e_total = max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_peak = sms * 128 * f_max * 1e6 / 1e12
+    achieved = 6 * cells / (kernel_ms / 1e3) / 1e12
+    line = {
+        "metric": f"{args.join} Gcells/s (FP32-mixed)",
+        "value": replica_value(world, cells, args.steps, total_ms), "unit": "Gcells/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)", "data": "synthetic",
+        "config": {"workload": desc, "cells": cells,
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
+                     "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
+                     "frac": achieved / issue_peak, "traffic": None, "kernel_ms": kernel_ms},
+        "e2e": {"value": replica_value(world, cells, args.steps, e2e_total), "unit": "Gcells/s",
+                "h2d_bytes_per_step": int(sum(v.nbytes for v in inputs)),
+                "d2h_bytes_per_step": int(out_bytes)},
+        "gpu_launches": 11 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,7 +635,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
-    ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss"), default="self")
+    ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss", "ab", "batched", "pan"),
+                    default="self")
     # long aliases: under torchrun, --n / --m prefix-match the launcher's own options
     ap.add_argument("--n", "--series-length", dest="n", type=int, default=N_DEFAULT)
     ap.add_argument("--m", "--window", dest="m", type=int, default=M_DEFAULT)
@@ -538,7 +654,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
-        (run_fluss if args.join == "fluss" else run_ours)(args, world, rank, local)
+        run = {"fluss": run_fluss, "ab": run_family, "batched": run_family,
+               "pan": run_family}.get(args.join, run_ours)
+        run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
