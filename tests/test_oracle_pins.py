@@ -83,7 +83,8 @@ def _scipy_profile(x, m, excl=None, inclusive=False, y=None, side=0, diag_ok=Non
     mp = D[np.arange(len(D)), pi]
     pi = np.where(np.isinf(mp), -1, pi)
     srt = np.sort(D, axis=1)
-    gap = srt[:, 1] - srt[:, 0] if D.shape[1] > 1 else np.full(len(D), np.inf)
+    with np.errstate(invalid="ignore"):            # inf - inf where a row has no neighbour
+        gap = srt[:, 1] - srt[:, 0] if D.shape[1] > 1 else np.full(len(D), np.inf)
     return mp, pi, gap
 
 
