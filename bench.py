@@ -60,11 +60,18 @@ TILE_KERNEL_SOURCES = ("internal.cuh", "cand_f32.cuh", "join_tile.cuh", "join_fp
 
 
 def csrc_digest() -> str:
+    """Digest of the tile kernel's code (comments and blank lines left out, so
+    that editing a comment does not void a profile)."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1904_12626_gb300", "csrc")
     for f in TILE_KERNEL_SOURCES:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(d, f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+        h.update(f.encode() + code.encode())
     return h.hexdigest()[:16]
 
 

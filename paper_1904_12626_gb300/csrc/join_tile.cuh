@@ -22,17 +22,22 @@
 // that the lanes' strided loads fall in distinct banks.
 //
 // Maxima without per-cell index bookkeeping.  Each row and each column
-// carries a threshold: the best correlation already merged into that index's
-// key (kept in the .w lane of the packed statistics, staged with them; +inf
-// for flat windows, whose answer is closed-form).  The fast path only asks, per cell,
-// "is rho >= the row's threshold or the column's threshold?" (2 compares,
-// OR-ed into one predicate), so a cell costs 2 FMA + 2 MUL + 2 compares.
-// When any lane of the warp saw a hit in a group of D rows, the warp replays
-// that group from the saved covariances with the same arithmetic (so the
-// correlations are bit-identical) and, for each hit, merges the packed key
-// (order-preserving correlation bits, inverted index) into the global key
-// array with an atomic max, so ties resolve to the lowest index whatever the
-// order tiles run in.  After warm-up almost no group hits.
+// carries a threshold: a lower bound of the best correlation its key already
+// holds (kept in the .w lane of the packed statistics, staged with them; +inf
+// for flat windows, whose answer is closed-form; keys start seeded).  The
+// fast path (fast_subchunk) only asks, per cell, "is rho >= the row's
+// threshold or the column's threshold?" (2 compares OR-ed into one
+// predicate), so a cell costs 2 FMA + 2 MUL + 2 compares.  A group of D rows
+// in which any lane hit is recorded with its starting covariances; after
+// each sub-chunk of kQueue groups the recorded groups are replayed with the
+// same arithmetic and bookkeeping: the FP32-mixed instantiation reduces the
+// group to certified candidates (replay_group_f32, keys in cand_f32.cuh), the
+// FP64 one merges (correlation, inverted index) keys by 128-bit CAS
+// (replay_group).  Either way ties resolve to the lowest index whatever the
+// order tiles run in.
+//
+// Non-normalised distance (RAW): the same loop ranks cells by the score
+// q - h_i - h_j (2 subtractions instead of the 2 multiplies), see internal.cuh.
 //
 // Anchors.  The first covariance of each diagonal in a tile, and every
 // `anchor_every` rows after it, is an exact FP64 dot product of the two
@@ -64,8 +69,10 @@ __device__ __forceinline__ Key128 cas128(Key128 *a, Key128 cmp, Key128 nv)
 
 struct TraitsF32 {
     // The fast path compares an upper bound of the correlation (the covariance
-    // carries a bias equal to a bound on its accumulated rounding error) and
-    // every candidate is verified exactly before it reaches a key.
+    // carries a bias equal to a bound on its accumulated rounding error); a
+    // candidate reaches its key with its bounds, and is compared exactly only
+    // where the bounds cannot decide (see cand_f32.cuh).  Packed is the
+    // (value, inverted index) word the replay ranks a row's cells by.
     static constexpr bool kBias = true;
     static constexpr float kEps = 1.1920929e-7f;          // 2^-23
     using T = float;
