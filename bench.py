@@ -344,7 +344,7 @@ def run_ours(args, world, rank, local):
     api.device_status(ws)
     total_ms = max_over_ranks(sum(step_ms), world)
     kernel_ms = max_over_ranks(statistics.mean(kern_ms), world)
-    if anytime:                # the tile kernel runs twice per step: judge the whole step
+    if anytime:                # the tile kernel runs twice per step: rate the whole step
         kernel_ms = total_ms / args.steps
     value = replica_value(world, cells, args.steps, total_ms)
 
@@ -536,6 +536,7 @@ def run_family(args, world, rank, local):
     lib = _lib.load()
     _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    kw: dict = {}                   # tile configuration (the library's defaults unless --tune)
     if args.join == "ab":
         m = 512
         a_np = synth.random_walk(1 << 21, seed=51, dtype=np.float32)
@@ -545,7 +546,7 @@ def run_family(args, world, rank, local):
         inputs = [a_np, b_np]
         desc = f"AB-join, 2^21 random walk x 2^19 walk/white-noise mix with flat stretches, m={m}"
         def call(xs):
-            return api.abjoin(xs[0], xs[1], m, "fp32")
+            return api.abjoin(xs[0], xs[1], m, "fp32", **kw)
         out_bytes = 16 * (la + lb)
     elif args.join == "batched":
         values, offsets, ms = synth.ragged_batch(4096, seed=55)
@@ -559,7 +560,7 @@ def run_family(args, world, rank, local):
         max_m = int(ms.max())
         desc = "batched self-joins, 4096 random walks of 1000..65536 samples, m in {32,64,128}"
         def call(xs):
-            mp, pi, _ = api.batched(xs[0], o_t, m_t, max_m=max_m)
+            mp, pi, _ = api.batched(xs[0], o_t, m_t, max_m=max_m, **kw)
             return mp, pi
         out_bytes = 16 * len(values)
     else:
@@ -570,9 +571,22 @@ def run_family(args, world, rank, local):
         inputs = [x_np]
         desc = "pan profile, 2^16 random walk, 64 window sizes 16..1024"
         def call(xs):
-            return api.pan(xs[0], ms)
+            return api.pan(xs[0], ms, **kw)
         out_bytes = 16 * len(ms) * (n - int(ms.min()) + 1)
     dev_in = [torch.from_numpy(v).cuda() for v in inputs]
+    tile = {"tuned": False}
+    if args.tune:                   # untimed: choose the tile configuration on this input
+        from paper_1904_12626_gb300.tune import Tuner
+        tuner = Tuner(args.tune_cache or None, warmup=0, reps=1)   # the check run warms up
+        if args.join == "ab":
+            kw.update(tuner.abjoin(dev_in[0], dev_in[1], m))
+        elif args.join == "batched":
+            kw.update(tuner.batched(dev_in[0], o_t, m_t, max_m=max_m))
+        else:
+            kw.update(tuner.pan(dev_in[0], ms))
+        ch = tuner.last
+        tile = {"tuned": True, **kw, "tuner_default_ms": ch.default_ms, "tuner_ms": ch.ms,
+                "candidates_timed": ch.measured}
     for _ in range(args.warmup):
         call(dev_in)
     torch.cuda.synchronize()
@@ -621,7 +635,7 @@ def run_family(args, world, rank, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)", "data": "synthetic",
-        "config": {"workload": desc, "cells": cells,
+        "config": {"workload": desc, "cells": cells, "tile": tile,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
@@ -652,6 +666,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=12.0)
+    ap.add_argument("--tune", action="store_true",
+                    help="--join ab | batched | pan: autotune the tile configuration first (untimed)")
+    ap.add_argument("--tune-cache", default="", help="JSON cache for --tune (default: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
