@@ -177,7 +177,8 @@ def workload(n: int, m: int):
 
 def cpu_oracle_rate(x, m: int, E: int, target_s: float, rows_min: int = 8):
     """Time the CPU oracle on a seeded sample of rows; returns
-    (cells_per_s of the whole job extrapolated, rows, seconds, cores)."""
+    (cells_per_s of the whole job extrapolated, rows, seconds, cores, results),
+    results = (row indices, MP, PI, second-best distance) of the sample."""
     import numpy as np
 
     import oracle
@@ -188,19 +189,37 @@ def cpu_oracle_rate(x, m: int, E: int, target_s: float, rows_min: int = 8):
     l = len(x64) - m + 1
     cells = selfjoin_cells(l, E)
     rows = max(rows_min, cores)
+    r0 = synth.sample_rows(l, rows, seed=99)
     t0 = time.perf_counter()
-    oracle.selfjoin(x64, m, rows=synth.sample_rows(l, rows, seed=99))
+    res = [(r0, *oracle.selfjoin(x64, m, rows=r0))]
     dt = time.perf_counter() - t0
     if dt < target_s:
         more = int(rows * (target_s - dt) / max(dt, 1e-3))
         more = max(0, min(more, 64 * cores))
         if more:
+            r1 = synth.sample_rows(l, more, seed=100)
             t1 = time.perf_counter()
-            oracle.selfjoin(x64, m, rows=synth.sample_rows(l, more, seed=100))
+            res.append((r1, *oracle.selfjoin(x64, m, rows=r1)))
             dt2 = time.perf_counter() - t1
             rows, dt = rows + more, dt + dt2
     per_row = dt / rows
-    return cells / (per_row * l), rows, dt, cores
+    results = tuple(np.concatenate([r[k] for r in res]) for k in range(4))
+    return cells / (per_row * l), rows, dt, cores, results
+
+
+def accuracy(results, mp, pi, gap: float = 1e-3) -> dict:
+    """Error of a GPU profile against the oracle on the oracle's rows: the
+    largest |dMP|, and whether PI is identical on every row whose best and
+    second-best distances differ by more than `gap`."""
+    rows, mo, po, so = results
+    g_mp, g_pi = np.asarray(mp)[rows], np.asarray(pi)[rows]
+    fin = np.isfinite(mo)
+    with np.errstate(invalid="ignore"):
+        sep = fin & ((so - mo) > gap)
+    return {"max_abs_dmp": float(np.max(np.abs(g_mp[fin] - mo[fin]))) if fin.any() else 0.0,
+            "finite_pattern_equal": bool(np.array_equal(np.isfinite(g_mp), fin)),
+            "separated_rows": int(sep.sum()),
+            "pi_equal_on_separated": bool(np.array_equal(g_pi[sep], po[sep]))}
 
 
 def run_reference(args, world, rank):
@@ -216,7 +235,7 @@ def run_reference(args, world, rank):
         cpu_oracle_rate(x, args.m, E, target_s=args.ref_step_s / 4)
     rates, rows_total, secs = [], 0, 0.0
     for _ in range(args.steps):
-        r, rows, dt, cores = cpu_oracle_rate(x, args.m, E, target_s=args.ref_step_s)
+        r, rows, dt, cores, _ = cpu_oracle_rate(x, args.m, E, target_s=args.ref_step_s)
         rates.append(r)
         rows_total += rows
         secs += dt
@@ -369,6 +388,7 @@ def run_ours(args, world, rank, local):
         ms64 = max_over_ranks(statistics.mean(t64), world)
         fp64 = {"value": cells / (ms64 / 1e3) / 1e9, "unit": "Gcells/s", "ms_per_step": ms64,
                 "kernel_ms": kms.value}
+        out64 = [t.cpu().numpy() for t in api.selfjoin(x, m, 0.5, "fp64", ws=ws64)]
         del ws64
 
     # end to end through the public API: pinned host input in, MP/PI back to host
@@ -426,12 +446,20 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
-    if not args.skip_cpu:
-        rate, rows, secs, cores = cpu_oracle_rate(x_np, m, E, target_s=args.cpu_seconds)
+    if not args.skip_cpu and world == 1:
+        rate, rows, secs, cores, results = cpu_oracle_rate(x_np, m, E, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gcells/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"{rows} seeded rows of the n={n} self-join in {secs:.1f} s, "
                                           f"extrapolated to all {l} rows"}
+        if not (lr or anytime or raw):
+            # error against the oracle on the same rows, FP32-mixed beside all-FP64
+            acc = {"rows": int(rows), "gap": 1e-3, "tolerance": {"fp32_mixed": 1e-3, "fp64": 1e-9},
+                   args.prec if args.prec == "fp64" else "fp32_mixed":
+                       accuracy(results, host_out[0].numpy(), host_out[1].numpy())}
+            if fp64 is not None:
+                acc["fp64"] = accuracy(results, *out64)
+            line["accuracy"] = acc
     print(json.dumps(line), flush=True)
 
 
