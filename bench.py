@@ -548,12 +548,139 @@ def run_fluss(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_grad(args, world, rank, local):
+    """--join grad: one differentiable step on a 2^16 random walk (float32,
+    m = 128): the self-join forward (FP32-mixed), loss = sum(MP) + mean of
+    the 16 largest MP values, and the backward kernel's scatter of the
+    closed-form gradient through the argmin pairs.  The step is timed whole
+    (forward, PyTorch's loss ops, backward); the tile kernel and the
+    backward call are also timed alone."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, build, synth
+    build.build()
+    api.init()
+    lib = _lib.load()
+    _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
+    n, m = 1 << 16, 128
+    E = math.ceil(0.5 * m)
+    l = n - m + 1
+    cells = selfjoin_cells(l, E)
+    x_np = synth.random_walk(n, seed=58, dtype=np.float32)
+    x = torch.from_numpy(x_np).cuda().requires_grad_(True)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    kms = ctypes.c_float()
+
+    def step(xx):
+        prof, _ = api.matrix_profile(xx, m)
+        loss = prof.sum() + prof.topk(16).values.mean()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        x.grad = None
+        step(x)
+    torch.cuda.synchronize()
+    times, kern = [], []
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            x.grad = None
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            step(x)
+            e.record()
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+            _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+            kern.append(kms.value)
+    barrier(world)
+    total_ms = max_over_ranks(sum(times), world)
+    kernel_ms = max_over_ranks(statistics.mean(kern), world)
+    # the backward call alone (convert, window statistics, scatter kernel)
+    with torch.no_grad():
+        prof, pi = api.selfjoin(x.detach(), m)
+        g = torch.ones_like(prof)
+        g[torch.topk(prof, 16).indices] += 1.0 / 16
+    bws = api.workspace(lib.mp_backward_workspace_bytes(n, m), x.device)
+    bwd = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        api.backward(x.detach(), m, pi, g, ws=bws)
+        e.record()
+        e.synchronize()
+        if it >= args.warmup:
+            bwd.append(s.elapsed_time(e))
+    api.device_status(bws)
+    bwd_ms = max_over_ranks(statistics.mean(bwd), world)
+    # end to end: pinned host series in, loss and gradient back to pinned host memory
+    xh = torch.from_numpy(x_np).pin_memory()
+    gh = torch.empty(n, dtype=torch.float32).pin_memory()
+    lh = torch.empty((), dtype=torch.float32).pin_memory()
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        xd = xh.to("cuda", non_blocking=True).requires_grad_(True)
+        loss = step(xd)
+        gh.copy_(xd.grad, non_blocking=True)
+        lh.copy_(loss.detach(), non_blocking=True)
+        e.record()
+        e.synchronize()
+        if it >= args.warmup:
+            e2e.append(s.elapsed_time(e))
+    e2e_total = max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    issue_peak = sms * 128 * f_max * 1e6 / 1e12
+    achieved = 6 * cells / (kernel_ms / 1e3) / 1e12
+    line = {
+        "metric": "differentiable self-join step (forward + backward) Gcells/s @n=2^16,m=128 "
+                  "(FP32-mixed forward, FP64 backward)",
+        "value": replica_value(world, cells, args.steps, total_ms), "unit": "Gcells/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 forward (FP64 stats/anchors/refine), f64 backward",
+        "data": "synthetic",
+        "config": {"workload": f"random walk n={n} float32, m={m}, loss = sum(MP) + mean(top-16 MP)",
+                   "cells": cells, "l2": "flushed between timed steps (512 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
+                     "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
+                     "frac": achieved / issue_peak, "traffic": None,
+                     "kernel": "join_tile_kernel<TraitsFP32> variant 0 (forward)",
+                     "kernel_ms": kernel_ms},
+        "backward": {"ms": bwd_ms, "rows": l, "fp64_atomic_adds": 2 * m * l,
+                     "atomic_adds_per_s": 2 * m * l / (bwd_ms / 1e3)},
+        "e2e": {"value": replica_value(world, cells, args.steps, e2e_total), "unit": "Gcells/s",
+                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n + 4},
+        # forward: the eleven launches of an FP32-mixed join; backward: convert,
+        # window statistics, scatter
+        "gpu_launches": 14 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_family(args, world, rank, local):
     """--join ab | batched | pan: the other join families at their parity-test
     sizes (AB: a 2^21 walk against a 2^19 walk / white-noise mix with flat
     stretches, m = 512; batched: 4096 ragged walks of 1000..65536 samples,
     m in {32, 64, 128}; pan: a 2^16 walk over 64 window sizes 16..1024),
-    FP32-mixed, L2 flushed between steps, timed like the self-join."""
+    FP32-mixed, L2 flushed between steps, timed like the self-join.  The
+    autotuner first chooses the tile configuration on the same input
+    (untimed; --no-tune keeps the library's defaults)."""
     import ctypes
 
     import torch
@@ -564,7 +691,7 @@ def run_family(args, world, rank, local):
     lib = _lib.load()
     _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    kw: dict = {}                   # tile configuration (the library's defaults unless --tune)
+    kw: dict = {}                   # tile configuration (the library's defaults with --no-tune)
     if args.join == "ab":
         m = 512
         a_np = synth.random_walk(1 << 21, seed=51, dtype=np.float32)
@@ -603,7 +730,7 @@ def run_family(args, world, rank, local):
         out_bytes = 16 * len(ms) * (n - int(ms.min()) + 1)
     dev_in = [torch.from_numpy(v).cuda() for v in inputs]
     tile = {"tuned": False}
-    if args.tune:                   # untimed: choose the tile configuration on this input
+    if args.tune:                   # untimed: the autotuner chooses the tile configuration
         from paper_1904_12626_gb300.tune import Tuner
         tuner = Tuner(args.tune_cache or None, warmup=0, reps=1)   # the check run warms up
         if args.join == "ab":
@@ -684,7 +811,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--prec", default="fp32")
-    ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss", "ab", "batched", "pan"),
+    ap.add_argument("--join", choices=("self", "lr", "anytime", "raw", "fluss", "ab", "batched", "pan",
+                                       "grad"),
                     default="self")
     # long aliases: under torchrun, --n / --m prefix-match the launcher's own options
     ap.add_argument("--n", "--series-length", dest="n", type=int, default=N_DEFAULT)
@@ -694,9 +822,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=12.0)
-    ap.add_argument("--tune", action="store_true",
-                    help="--join ab | batched | pan: autotune the tile configuration first (untimed)")
-    ap.add_argument("--tune-cache", default="", help="JSON cache for --tune (default: none)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="--join ab | batched | pan: keep the library's default tile configuration "
+                         "(by default the autotuner chooses it first, untimed)")
+    ap.add_argument("--tune-cache", default="",
+                    help="JSON cache of the autotuner's choices (default: in memory only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -707,7 +837,7 @@ def main():
         run_reference(args, world, rank)
     else:
         run = {"fluss": run_fluss, "ab": run_family, "batched": run_family,
-               "pan": run_family}.get(args.join, run_ours)
+               "pan": run_family, "grad": run_grad}.get(args.join, run_ours)
         run(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
