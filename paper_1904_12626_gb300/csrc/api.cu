@@ -102,6 +102,37 @@ mp_status resolve(const mp_config *cfg, TileCfg *t)
     return MP_OK;
 }
 
+// Row-tile height of a join whose caller left it to the library.  The tile
+// kernel is persistent: every CTA takes tickets until none is left, so a join
+// ends when its busiest CTA does, up to one tile after the average.  The
+// default height has the fewest FP64 anchors (m multiply-adds per diagonal
+// per tile); a join so small that one such tile exceeds a quarter of a CTA's
+// share of the cells gets the height halved, down to kMinFitRows.  Only the
+// speed changes: every height gives the same neighbours.
+constexpr int kFitTilesPerCta = 4;
+constexpr int kMinFitRows = 1024;
+
+void fit_tile_rows(const mp_config *cfg, TileCfg *t, double cells, const DeviceInfo *d)
+{
+    if (cfg->tile_rows > 0 || !(cells > 0.0) || d == nullptr) return;
+    const int bps = t->raw ? (t->fp64 ? d->f64_raw_bps : d->f32_raw_bps)
+                           : (t->fp64 ? d->f64_bps[t->variant] : d->f32_bps[t->variant]);
+    if (bps <= 0 || d->sms <= 0) return;
+    const double share = cells / ((double)d->sms * (double)bps);
+    long long tr = t->tile_rows;
+    while (tr > kMinFitRows && (double)tr * t->tile_diags * kFitTilesPerCta > share) tr >>= 1;
+    tr = ceil_div(tr, t->chunk_rows) * t->chunk_rows;
+    t->tile_rows = (int)tr;
+    if (t->anchor_every >= t->tile_rows) t->anchor_every = 0;
+}
+
+// admissible pairs of a self-join (an estimate for the inclusive zone)
+double self_cells(int64_t n, int32_t m, double ez)
+{
+    const double l = (double)(n - m + 1), e = std::ceil(ez * (double)m);
+    return l > e ? (l - e) * (l - e + 1.0) / 2.0 : 0.0;
+}
+
 // Workspace layout shared by every join.
 struct LayoutReq {
     long long nx = 0;        // FP64 copy of the input values
@@ -398,6 +429,7 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
     F.mp_a = mp; F.pi_a = (long long *)pi; F.out_stride = 0;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
+    fit_tile_rows(cfg, &t, self_cells(n, m, cfg->ez), d);
     return run_join(L, r, t, n - m + 1, d, st);
 }
 
@@ -430,6 +462,7 @@ mp_status mp_anytime_begin(const void *x, int32_t dtype, int64_t n, const mp_con
     F.mp_a = nullptr; F.pi_a = nullptr; F.out_stride = 0;   // outputs bound per run
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
+    fit_tile_rows(cfg, &t, self_cells(n, m, cfg->ez), d);
     if ((s = prepare_join(L, r, t, n - m + 1, st)) != MP_OK) return s;
     MP_CU(launch_permute_bands(seed, L.bands, L.tile_prefix, L.scratch, r.max_bands, L.hdr, st));
     return MP_OK;
@@ -453,6 +486,7 @@ mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, doubl
     cudaStream_t st = (cudaStream_t)stream;
     MP_CU(launch_bind_outputs(L.fins, mp, (long long *)pi, st));
     MP_CU(launch_anytime_window(fraction, L.tile_prefix, L.hdr, st));
+    fit_tile_rows(cfg, &t, self_cells(n, m, cfg->ez), d);      // as planned by the begin call
     return execute_join(L, r, t, n - m + 1, d, st);
 }
 
@@ -513,6 +547,7 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
     F.mp_b = mp_left; F.pi_b = (long long *)pi_left;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
+    fit_tile_rows(cfg, &t, self_cells(n, m, cfg->ez), d);
     return run_join(L, r, t, n - m + 1, d, st);
 }
 
@@ -552,6 +587,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
     const long long la = na - m + 1, lb = nb - m + 1;
+    fit_tile_rows(cfg, &t, (double)la * (double)lb, d);
     return run_join(L, r, t, la > lb ? la : lb, d, st);
 }
 
@@ -595,6 +631,9 @@ mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int
     F.mp_a = pan; F.pi_a = (long long *)pi; F.out_stride = n - mmin + 1;
     F.sets = L.sets; F.probs = L.probs; F.fins = L.fins;
     MP_CU(launch_family_descs(F, st));
+    double cells = 0.0;
+    for (int k = 0; k < nm; ++k) cells += self_cells(n, ms[k], cfg->ez);
+    fit_tile_rows(cfg, &t, cells, d);
     return run_join(L, r, t, n - mmin + 1, d, st);
 }
 

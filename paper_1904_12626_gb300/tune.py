@@ -7,7 +7,8 @@ Three knobs set how fast a join runs and never what it returns:
   per CTA; ``mp_variant_count`` / ``mp_variant_info``);
 * the row-tile height, ``tile_rows``: the rows one ticket of the work queue
   walks down its band, so the queue's granularity and the distance between
-  exact FP64 anchors;
+  exact FP64 anchors (0: the library's choice, which shortens the default
+  height for small joins so that the persistent grid stays balanced);
 * the re-anchor interval K, ``anchor_every``: further exact FP64 anchors
   inside a tile (the exact first dot product, then reuse, of STOMP,
   Sec. 3.3.2).  A shorter interval narrows the error bound the FP32
@@ -19,9 +20,11 @@ batched, pan), the window, the sizes and the device, so the tuner measures
 instead of guessing.  It times candidates on the caller's input with CUDA
 events on the current stream, in three stages:
 
-1. every variant at the default tile height and no extra anchors;
+1. every variant at the library's tile height and no extra anchors;
 2. the two fastest variants at each tile height of the precision's ladder;
-3. the fastest pair at K = tile height / 2, / 4, / 8.
+3. the fastest pair at K = tile height / 2, / 4, / 8 (the default height's
+   fractions when the library's height won; the library drops an interval
+   not shorter than the height it runs).
 
 It keeps the fastest candidate whose output agrees with the default
 configuration's within the precision's error budget (``|dMP| <= 1e-3`` for
@@ -45,7 +48,7 @@ import torch
 
 CACHE_VERSION = 1
 TOL = {"fp32": 1e-3, "fp64": 1e-9}
-TILE_ROWS = {"fp32": (4096, 8192, 16384, 32768), "fp64": (1024, 2048, 4096, 8192)}
+TILE_ROWS = {"fp32": (1024, 2048, 4096, 8192, 16384, 32768), "fp64": (1024, 2048, 4096, 8192)}
 DEFAULT_TILE_ROWS = {"fp32": 16384, "fp64": 4096}   # the library's defaults
 ANCHOR_DIVISORS = (2, 4, 8)
 TOP_VARIANTS = 2
@@ -54,8 +57,8 @@ TOP_VARIANTS = 2
 @dataclass(frozen=True)
 class Candidate:
     """One tile configuration, in the library's resolved form (tile_rows and
-    anchor_every whole multiples of the variant's chunk rows; 0 = no extra
-    anchors)."""
+    anchor_every whole multiples of the variant's chunk rows; tile_rows 0 =
+    the library's choice; anchor_every 0 = no extra anchors)."""
     variant: int
     tile_rows: int
     anchor_every: int
@@ -72,9 +75,12 @@ def _ceil_to(v: int, q: int) -> int:
 def resolve(variant: int, chunk_rows: int, tile_rows: int, anchor_every: int) -> Candidate:
     """The configuration the library runs for these arguments: both lengths
     rounded up to whole chunks; an interval not shorter than the tile means
-    anchors at tile starts only."""
-    tr = _ceil_to(tile_rows, chunk_rows)
+    anchors at tile starts only (with tile_rows 0 the library settles the
+    height, and that rule, per call)."""
     k = _ceil_to(anchor_every, chunk_rows) if anchor_every > 0 else 0
+    if tile_rows <= 0:
+        return Candidate(variant, 0, k)
+    tr = _ceil_to(tile_rows, chunk_rows)
     return Candidate(variant, tr, 0 if k >= tr else k)
 
 
@@ -90,7 +96,7 @@ class Space:
         return dict(self.variants)[variant]
 
     def stage1(self) -> list[Candidate]:
-        return _unique(resolve(v, rc, self.default_tile_rows, 0) for v, rc in self.variants)
+        return _unique(resolve(v, rc, 0, 0) for v, rc in self.variants)
 
     def stage2(self, variants: Iterable[int]) -> list[Candidate]:
         return _unique(resolve(v, self.chunk_rows(v), tr, 0)
@@ -98,8 +104,9 @@ class Space:
 
     def stage3(self, best: Candidate) -> list[Candidate]:
         rc = self.chunk_rows(best.variant)
-        return _unique(resolve(best.variant, rc, best.tile_rows, best.tile_rows // d)
-                       for d in ANCHOR_DIVISORS if best.tile_rows // d >= rc)
+        tr = best.tile_rows or self.default_tile_rows
+        return _unique(resolve(best.variant, rc, best.tile_rows, tr // d)
+                       for d in ANCHOR_DIVISORS if tr // d >= rc)
 
 
 def _unique(cands: Iterable[Candidate]) -> list[Candidate]:
@@ -115,8 +122,8 @@ def staged_search(space: Space, measure: Callable[[Candidate], float | None]
     """The three stages above.  `measure` returns a candidate's time in ms,
     or None when it is rejected (unsupported here, or its output disagrees);
     each candidate is measured once.  The default configuration (variant 0
-    at the default height) is measured first and is the answer when nothing
-    else is faster; ties go to the earlier-measured candidate."""
+    at the library's height) is measured first and is the answer when
+    nothing else is faster; ties go to the earlier-measured candidate."""
     times: dict[Candidate, float | None] = {}
 
     def timed(c: Candidate) -> float | None:
@@ -128,7 +135,7 @@ def staged_search(space: Space, measure: Callable[[Candidate], float | None]
         ok = [c for c in _unique(cands) if timed(c) is not None]
         return sorted(ok, key=lambda c: (times[c], list(times).index(c)))
 
-    default = resolve(space.variants[0][0], space.variants[0][1], space.default_tile_rows, 0)
+    default = resolve(space.variants[0][0], space.variants[0][1], 0, 0)
     if timed(default) is None:
         raise RuntimeError("the default tile configuration was rejected")
     s1 = ranked([default] + space.stage1())

@@ -22,14 +22,20 @@ def test_resolve_rounds_like_the_library():
     assert tune.resolve(0, 512, 4096, 4096) == Candidate(0, 4096, 0)     # K >= tile: tile starts only
     assert tune.resolve(0, 512, 4096, 3900) == Candidate(0, 4096, 0)     # rounds up to the tile
     assert tune.resolve(0, 512, 4096, 511) == Candidate(0, 4096, 512)
+    # height 0: the library's own choice, the interval still in whole chunks
+    assert tune.resolve(0, 512, 0, 0) == Candidate(0, 0, 0)
+    assert tune.resolve(0, 512, 0, 3000) == Candidate(0, 0, 3072)
 
 
 def test_stages_enumerate_distinct_candidates():
-    assert len(SPACE.stage1()) == 4
+    assert SPACE.stage1() == [Candidate(v, 0, 0) for v in range(4)]
     s2 = SPACE.stage2([1, 3])
     assert len(s2) == 8 and len(set(s2)) == 8
     s3 = SPACE.stage3(Candidate(2, 4096, 0))
     assert s3 == [Candidate(2, 4096, 2048), Candidate(2, 4096, 1024), Candidate(2, 4096, 512)]
+    # the library's height won: fractions of the default height
+    assert SPACE.stage3(Candidate(1, 0, 0)) == [Candidate(1, 0, 8192), Candidate(1, 0, 4096),
+                                                Candidate(1, 0, 2048)]
     # intervals shorter than a chunk are left out, equal ones merge
     small = Space([(0, 512)], (1024,), 1024)
     assert small.stage3(Candidate(0, 1024, 0)) == [Candidate(0, 1024, 512)]
@@ -38,7 +44,7 @@ def test_stages_enumerate_distinct_candidates():
 def _cost(c: Candidate) -> float:
     """A separable cost with its minimum at variant 2, 8192 rows, K = 2048."""
     v = {0: 10.0, 1: 12.0, 2: 9.0, 3: 11.0}[c.variant]
-    t = {4096: 1.0, 8192: 0.0, 16384: 0.5, 32768: 2.0}[c.tile_rows]
+    t = {0: 0.5, 4096: 1.0, 8192: 0.0, 16384: 0.5, 32768: 2.0}[c.tile_rows]
     k = {0: 0.3, 4096: 0.2, 2048: 0.0, 1024: 0.4}[c.anchor_every]
     return v + t + k
 
@@ -52,11 +58,11 @@ def test_staged_search_finds_separable_optimum():
     best, times = tune.staged_search(SPACE, measure)
     assert best == Candidate(2, 8192, 2048)
     assert len(seen) == len(set(seen))                  # each candidate timed once
-    assert seen[0] == Candidate(0, 16384, 0)            # the default first
+    assert seen[0] == Candidate(0, 0, 0)                # the library's default first
     assert len(seen) <= 4 + 2 * 4 + 3
     # the second-best variant of stage 1 (0) was tried at every height
-    assert {c.tile_rows for c in seen if c.variant == 0} == {4096, 8192, 16384, 32768}
-    assert not any(c.variant in (1, 3) and c.tile_rows != 16384 for c in seen)
+    assert {c.tile_rows for c in seen if c.variant == 0} == {0, 4096, 8192, 16384, 32768}
+    assert not any(c.variant in (1, 3) and c.tile_rows != 0 for c in seen)
 
 
 def test_staged_search_never_picks_rejected_and_keeps_default_on_ties():
@@ -65,8 +71,8 @@ def test_staged_search_never_picks_rejected_and_keeps_default_on_ties():
             return None                                 # unsupported / disagrees
         return 5.0
     best, times = tune.staged_search(SPACE, measure)
-    assert best == Candidate(0, 16384, 0)
-    assert times[Candidate(2, 16384, 0)] is None
+    assert best == Candidate(0, 0, 0)
+    assert times[Candidate(2, 0, 0)] is None
     with pytest.raises(RuntimeError):
         tune.staged_search(SPACE, lambda c: None)
 
@@ -137,7 +143,7 @@ def test_tuner_rejects_wrong_outputs_and_caches(tmp_path):
     ch = t.tune("k1", "fp32", False, fake.run)
     assert (ch.variant, ch.tile_rows, ch.anchor_every) == (2, 8192, 2048)   # not variant 3
     assert ch.ms == pytest.approx(_cost(Candidate(2, 8192, 2048)))
-    assert ch.default_ms == pytest.approx(_cost(Candidate(0, 16384, 0)))
+    assert ch.default_ms == pytest.approx(_cost(Candidate(0, 0, 0)))
     assert t.last == ch and t.measured == ch.measured > 0
     data = json.loads(path.read_text())
     assert data["version"] == tune.CACHE_VERSION and "k1" in data["entries"]
