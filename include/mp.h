@@ -76,8 +76,12 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * diagonal recurrence (MP_PREC_FP32_MIXED keeps stats, anchors and the
  * final distances in FP64).  anchor_every (K): rows between exact FP64
  * re-anchors of each diagonal's covariance; 0 = once per tile.  tile_rows
- * (TR): rows per tile; 0 = library default.  variant: compiled tile shape
- * (0 = default; see mp_variant_count/mp_variant_info).  flags: MP_FLAG_*.
+ * (TR): rows per tile; 0 = the library's choice (16384 FP32-mixed, 4096
+ * FP64, halved down to 1024 for joins too small to keep every CTA of the
+ * persistent grid busy with that many; mp_batched keeps the default).
+ * Both are rounded up to whole chunks of the variant.  variant: compiled
+ * tile shape (0 = default; see mp_variant_count/mp_variant_info).  These
+ * three set the speed only, never the neighbours found.  flags: MP_FLAG_*.
  */
 typedef struct {
     int32_t m;
