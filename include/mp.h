@@ -81,7 +81,9 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * persistent grid busy with that many; mp_batched keeps the default).
  * Both are rounded up to whole chunks of the variant.  variant: compiled
  * tile shape (0 = default; see mp_variant_count/mp_variant_info).  These
- * three set the speed only, never the neighbours found.  flags: MP_FLAG_*.
+ * three set the speed: the FP32-mixed path returns the same neighbours under
+ * every setting, the FP64 path may break ties closer than its rounding
+ * differently.  flags: MP_FLAG_*.
  */
 typedef struct {
     int32_t m;
