@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "join_tile.cuh"
+#include "launch_shape.cuh"
 
 namespace mpgb {
 namespace {
@@ -98,7 +99,8 @@ __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__re
 // ---- FP32 path, self-join sets: the same seeds by the diagonal recurrence ----
 //
 // The pairs (w, w + kmin) all lie on diagonal kmin, so instead of two dot
-// products per window a thread walks kSeedRun windows of that diagonal: an
+// products per window a thread walks a run of windows of that diagonal (at
+// most kSeedRun; shorter for short series, see launch_shape.cuh): an
 // exact FP64 dot product at the run's start, then the FP64 recurrence
 // c += df_w dg_j + df_j dg_w.  Window w offers j = w + kmin to its own key (its
 // right side) and j receives w (its left side); a key takes the larger value,
@@ -106,6 +108,8 @@ __global__ void seed_kernel(const StatSet *__restrict__ sets, const double *__re
 // (value, inverted index).  seed_finish_kernel completes the keys (exact: the
 // lower bound is the value) and the thresholds.
 constexpr int kSeedRun = 128;
+constexpr int kMinSeedRun = 16;
+constexpr int kSeedThreads = 32;
 
 __device__ __forceinline__ unsigned long long seed_pack(double r, long long idx)
 {
@@ -116,14 +120,14 @@ __device__ __forceinline__ unsigned long long seed_pack(double r, long long idx)
 
 __global__ void seed_diag_kernel(const StatSet *__restrict__ sets, const double *__restrict__ mu,
                                  const double *__restrict__ inv, const uint8_t *__restrict__ flat,
-                                 const D4 *__restrict__ s64, Key128 *keys)
+                                 const D4 *__restrict__ s64, Key128 *keys, int run)
 {
     const StatSet S = sets[blockIdx.y];
     if (S.l <= 0 || S.kmin < 0 || S.dir < 0) return;     // AB sets; left roles are filled here
     const StatSet Y = sets[S.partner];
     const long long k = S.kmin;
-    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kSeedRun;
-    long long wend = w0 + kSeedRun;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * run;
+    long long wend = w0 + run;
     if (wend > S.l) wend = S.l;
     if (wend > Y.l - k) wend = Y.l - k;                  // j = w + k must be a window
     if (w0 >= wend) return;
@@ -191,9 +195,10 @@ cudaError_t launch_seed(const StatSet *sets, int nsets, long long max_l, const d
     }
     // FP32 path: AB sets from a dot product each, self-join sets along diagonal kmin
     seed_kernel<false><<<grid, threads, 0, st>>>(sets, mu, inv, flat, s32, s64, k128, 1);
-    const long long runs = (max_l + kSeedRun - 1) / kSeedRun;
-    const dim3 gd((unsigned)((runs + 127) / 128), (unsigned)nsets);
-    seed_diag_kernel<<<gd, 128, 0, st>>>(sets, mu, inv, flat, s64, k128);
+    const int run = spread_run(max_l, nsets, kSeedThreads, kSeedRun, kMinSeedRun);
+    const long long runs = (max_l + run - 1) / run;
+    const dim3 gd((unsigned)((runs + kSeedThreads - 1) / kSeedThreads), (unsigned)nsets);
+    seed_diag_kernel<<<gd, kSeedThreads, 0, st>>>(sets, mu, inv, flat, s64, k128, run);
     seed_finish_kernel<<<grid, threads, 0, st>>>(sets, flat, s32, k128);
     return cudaGetLastError();
 }

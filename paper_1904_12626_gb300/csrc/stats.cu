@@ -9,7 +9,10 @@
 // dot product c (this is the dot-product reuse the paper credits to STOMP,
 // Sec. 3.3.2, written in covariance form).
 //
-// Each thread owns a run of consecutive windows.  It seeds the window sums
+// Each thread owns a run of consecutive windows (at most kWindowsPerThread;
+// shorter when a series is short, so that the blocks of kStatsThreads
+// threads still reach every SM: the work is FP64-bound, and the FP64 pipes
+// of idle SMs are lost).  It seeds the window sums
 // sum(x) and sum(x^2) of the run's first window with a direct double-double
 // (106-bit) summation and then slides them window to window, adding the
 // entering sample and subtracting the leaving one in double-double, so the
@@ -23,9 +26,13 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "launch_shape.cuh"
 
 namespace mpgb {
 namespace {
+
+constexpr int kStatsThreads = 32;      // one warp per block: short series spread over more SMs
+constexpr int kMinStatsRun = 4;
 
 struct dd {
     double hi, lo;
@@ -147,14 +154,14 @@ __global__ void convert_kernel(const T *__restrict__ x, long long n, double *__r
 }
 
 __global__ void stats_sets_kernel(const StatSet *__restrict__ sets, int nsets, long long total,
-                                  double *__restrict__ mu, double *__restrict__ inv,
+                                  int run, double *__restrict__ mu, double *__restrict__ inv,
                                   float4 *__restrict__ s32,
                                   D4 *__restrict__ s64, uint8_t *__restrict__ flat,
                                   double *__restrict__ set_acc)
 {
-    long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kWindowsPerThread;
+    long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * run;
     if (g >= total) return;
-    const long long gend = min(g + (long long)kWindowsPerThread, total);
+    const long long gend = min(g + (long long)run, total);
     int lo = 0, hi = nsets;                       // sets[lo].sbase <= g < sets[hi].sbase
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -225,13 +232,13 @@ __global__ void stats_sets_kernel(const StatSet *__restrict__ sets, int nsets, l
 }
 
 template <typename T>
-__global__ void stats_public_kernel(const T *__restrict__ x, long long l, int m,
+__global__ void stats_public_kernel(const T *__restrict__ x, long long l, int m, int run,
                                     double *mu, double *invn, double *df, double *dg,
                                     uint8_t *flat)
 {
-    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kWindowsPerThread;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * run;
     if (i >= l) return;
-    const long long iend = min(i + (long long)kWindowsPerThread, l);
+    const long long iend = min(i + (long long)run, l);
     walk_windows<T>(x, m, i, iend, [&](long long w, const WindowOut &o) {
         if (mu) mu[w] = o.mu;
         if (invn) invn[w] = o.invn;
@@ -242,6 +249,23 @@ __global__ void stats_public_kernel(const T *__restrict__ x, long long l, int m,
 }
 
 }  // namespace
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    return sms;
+}
+
+int spread_run(long long items, long long groups, int threads, int run, int min_run)
+{
+    const long long sms = sm_count();
+    auto blocks = [&](int r) { return groups * (((items + r - 1) / r + threads - 1) / threads); };
+    while (run > min_run && blocks(run / 2) <= sms) run /= 2;
+    return run;
+}
 
 cudaError_t launch_convert(const void *x, int dtype, long long n, double *x64, Hdr *hdr,
                            cudaStream_t st)
@@ -262,11 +286,11 @@ cudaError_t launch_stats_sets(const StatSet *sets, int nsets, long long total_in
                               cudaStream_t st)
 {
     if (total_index <= 0 || nsets <= 0) return cudaSuccess;
-    const int threads = 128;
-    const long long runs = (total_index + kWindowsPerThread - 1) / kWindowsPerThread;
-    const long long blocks = (runs + threads - 1) / threads;
-    stats_sets_kernel<<<(unsigned)blocks, threads, 0, st>>>(sets, nsets, total_index, mu, inv, s32,
-                                                             s64, flat, set_acc);
+    const int run = spread_run(total_index, 1, kStatsThreads, kWindowsPerThread, kMinStatsRun);
+    const long long runs = (total_index + run - 1) / run;
+    const long long blocks = (runs + kStatsThreads - 1) / kStatsThreads;
+    stats_sets_kernel<<<(unsigned)blocks, kStatsThreads, 0, st>>>(sets, nsets, total_index, run, mu,
+                                                                   inv, s32, s64, flat, set_acc);
     return cudaGetLastError();
 }
 
@@ -276,15 +300,15 @@ cudaError_t launch_stats_public(const void *x, int dtype, long long n, int m, do
 {
     const long long l = n - m + 1;
     if (l <= 0) return cudaSuccess;
-    const int threads = 128;
-    const long long runs = (l + kWindowsPerThread - 1) / kWindowsPerThread;
-    const long long blocks = (runs + threads - 1) / threads;
+    const int run = spread_run(l, 1, kStatsThreads, kWindowsPerThread, kMinStatsRun);
+    const long long runs = (l + run - 1) / run;
+    const long long blocks = (runs + kStatsThreads - 1) / kStatsThreads;
     if (dtype == MP_F32)
-        stats_public_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float *)x, l, m, mu,
-                                                                         invn, df, dg, flat);
+        stats_public_kernel<float><<<(unsigned)blocks, kStatsThreads, 0, st>>>(
+            (const float *)x, l, m, run, mu, invn, df, dg, flat);
     else
-        stats_public_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double *)x, l, m,
-                                                                          mu, invn, df, dg, flat);
+        stats_public_kernel<double><<<(unsigned)blocks, kStatsThreads, 0, st>>>(
+            (const double *)x, l, m, run, mu, invn, df, dg, flat);
     return cudaGetLastError();
 }
 
