@@ -53,6 +53,17 @@ def test_random_neighbours_follow_the_idealised_curve():
     assert ratio.std() < 0.03
 
 
+def test_edge_margin_by_hand():
+    """One arc 0 -> 9 over l = 10 positions (AC = 1 on 0..8) with edge 2: the
+    curve is 1 on the first and last two positions and AC / IAC on 2..7,
+    IAC[k] = 2 k (l - k) / l."""
+    pi = np.array([9, -1, -1, -1, -1, -1, -1, -1, -1, -1])
+    cac, _ = oracle.fluss(pi, m=1, num_segments=0, edge=2, seg_excl=1)
+    want = [1.0, 1.0, 1 / 3.2, 1 / 4.2, 1 / 4.8, 1 / 5.0, 1 / 4.8, 1 / 4.2, 1.0, 1.0]
+    np.testing.assert_allclose(cac, want, rtol=1e-15)
+    assert cac[2] < 1.0 and cac[7] < 1.0          # first and last positions outside the margin
+
+
 def test_segment_masking():
     cac = np.array([0.9, 0.5, 0.4, 0.45, 0.9, 0.9, 0.2, 0.9, 0.3, 0.9])
     seg = np.empty(4, dtype=np.int64)
