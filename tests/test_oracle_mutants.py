@@ -40,6 +40,16 @@ MUTANTS = {
     "raw_unsquared": ("                    acc += e * e;", "                    acc += fabs(e);"),
     "lr_sides_swapped": ("if ((J->side < 0 && j >= i) || (J->side > 0 && j <= i)) return 0;",
                          "if ((J->side > 0 && j >= i) || (J->side < 0 && j <= i)) return 0;"),
+    "cac_edge_off_by_one": ("if (k >= edge && k < l - edge && iac > 0.0) {",
+                            "if (k > edge && k < l - edge && iac > 0.0) {"),
+    "cac_unclamped": ("c = r < 1.0 ? r : 1.0;", "c = r;"),
+    "segment_tie_to_last": ("if (best < 0 || cac[k] < cac[best]) best = k;",
+                            "if (best < 0 || cac[k] <= cac[best]) best = k;"),
+    "second_not_shifted": ("                second = best;\n", ""),
+    "raw_missing_sqrt": ("                d = sqrt(acc);", "                d = acc;"),
+    "distance_uncapped": ("    return d > cap ? cap : d;", "    return d;"),
+    "segment_zone_inclusive": ("if (d < seg_excl || d == 0) masked = 1;",
+                               "if (d <= seg_excl || d == 0) masked = 1;"),
 }
 
 

@@ -130,6 +130,21 @@ def test_affine_copy_invariance():
     assert abs(oracle.distance(y, m, i, j) - 2 * math.sqrt(m)) <= 1e-9
 
 
+def test_distance_never_exceeds_the_bound():
+    """A negated copy is at distance 2 sqrt(m) exactly in exact arithmetic;
+    rounding may land just above, and the convention clamps d to [0, 2 sqrt(m)]
+    with no slack (20 seeded windows of random length, scale and offset: in
+    about half of them the unclamped FP64 value exceeds the bound)."""
+    for seed in range(20):
+        rng = np.random.default_rng(seed)
+        m = int(rng.integers(8, 300))
+        w = rng.standard_normal(m) * rng.uniform(0.1, 10) + rng.uniform(-100, 100)
+        x = np.concatenate([w, -w])
+        d = oracle.distance(x, m, 0, m)
+        assert d <= 2 * math.sqrt(m)
+        assert d >= 2 * math.sqrt(m) - 1e-9
+
+
 def test_distance_symmetry_bitwise():
     x = synth.random_walk(900, seed=21)
     a = synth.random_walk(400, seed=22)
