@@ -1,0 +1,132 @@
+"""The FP32-mixed path's error bias, checked against emulated FP32 rounding
+(no GPU).
+
+The tile kernel walks each diagonal with the covariance recurrence
+c(i,j) = c(i-1,j-1) + df_i dg_j + df_j dg_i in FP32 (two fused multiply-adds
+per cell, operands rounded to FP32) from an exact anchor, and adds to every
+covariance a bias E that bounds the rounding accumulated since the anchor:
+
+    E = 2 eps C sqrt(N + 16),  eps = 2^-23,
+    C = the largest, over the 512-row chunks since the anchor, of
+        s_R s_C + 2 (df_R dg_C + df_C dg_R),
+
+with s, df, dg the RMS over the chunk's rows (R) and over the columns it
+stages (C: the chunk's rows shifted by the band's first diagonal, plus the
+band width), and N the rows since the anchor.  Rounding errors of N steps add
+up like a random walk, so E is a statistical bound (about five standard
+deviations), not a worst case.  These tests emulate the recurrence in FP32
+(a product of two FP32 values is exact in FP64, so FP64 add + one rounding
+to FP32 is the fused multiply-add) against an FP64 recurrence, and check
+
+* that E covers the error on random walks;
+* that it must be the running maximum since the anchor: when the windows'
+  norms drop (random walk, then white noise), the absolute error built up
+  before the drop stays, and a bias from the current chunk alone is exceeded;
+* that an anchor at the drop resets the error, so the bias there could be
+  several times narrower.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1904_12626_gb300 import synth
+
+EPS32 = 2.0 ** -23
+CHUNK = 512
+
+
+def _stats(x, m):
+    """mean, centred norm, df, dg per window (FP64, straightforward)."""
+    l = len(x) - m + 1
+    win = np.lib.stride_tricks.sliding_window_view(x, m)
+    mu = win.mean(axis=1)
+    s = np.linalg.norm(win - mu[:, None], axis=1)
+    df = np.zeros(l)
+    dg = np.zeros(l)
+    df[1:] = (x[m:m + l - 1] - x[:l - 1]) / 2
+    dg[1:] = (x[m:m + l - 1] - mu[1:]) + (x[:l - 1] - mu[:-1])
+    return win, mu, s, df, dg
+
+
+def _walk(a, b, m, k0, width, rows, bias="running", anchor_rows=()):
+    """Walk diagonals k0..k0+width-1 (row i of a against column i+k of b) for
+    `rows` rows from an anchor at row 0; returns the largest error / bias
+    ratio per chunk, and the bias per chunk (correlation units of the
+    chunk's first cell, for comparisons)."""
+    winA, muA, sA, dfA, dgA = _stats(a, m)
+    winB, muB, sB, dfB, dgB = _stats(b, m)
+    ks = k0 + np.arange(width)
+
+    def exact(i):
+        return np.einsum("t,dt->d", winA[i] - muA[i], winB[i + ks] - muB[i + ks][:, None])
+
+    f32 = lambda v: np.asarray(v, np.float32).astype(np.float64)
+    c64 = exact(0)
+    c32 = c64.astype(np.float32)
+    e_c, steps = 0.0, 0
+    ratios, biases = [], []
+    for r in range(0, rows, CHUNK):
+        if r in anchor_rows:                       # exact covariance at row r - 1
+            c64 = exact(r - 1)
+            c32 = c64.astype(np.float32)
+            e_c, steps = 0.0, 0
+        R = slice(r, r + CHUNK)
+        C = slice(r + k0, r + k0 + CHUNK + width)
+        rms = lambda v: math.sqrt(float(np.mean(v * v)))
+        cur = rms(sA[R]) * rms(sB[C]) + 2 * (rms(dfA[R]) * rms(dgB[C]) + rms(dfB[C]) * rms(dgA[R]))
+        e_c = cur if bias == "current" else max(e_c, cur)
+        steps += CHUNK
+        E = 2.0 * EPS32 * e_c * math.sqrt(steps + 16)
+        worst = 0.0
+        for i in range(max(r, 1), r + CHUNK):
+            j = i + ks
+            c64 = c64 + dfA[i] * dgB[j] + dfB[j] * dgA[i]
+            c32 = (c32.astype(np.float64) + f32(dfA[i]) * f32(dgB[j])).astype(np.float32)
+            c32 = (c32.astype(np.float64) + f32(dfB[j]) * f32(dgA[i])).astype(np.float32)
+            worst = max(worst, float(np.abs(c32.astype(np.float64) - c64).max()) / E)
+        ratios.append(worst)
+        biases.append(E / (sA[r] * sB[r + k0]))
+    return np.array(ratios), np.array(biases)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bias_covers_fp32_rounding_on_random_walks(seed):
+    m = 256
+    a = synth.random_walk(12000, seed=seed)
+    b = synth.random_walk(12000, seed=seed + 100)
+    ratios, _ = _walk(a, b, m, k0=128, width=64, rows=8192)
+    assert ratios.max() < 1.0
+    assert ratios.max() > 0.02                     # and it is not vacuous
+
+
+def _drop_input(seed, m):
+    """rows: a random walk; columns: a random walk, then white noise (norm
+    about 10x smaller) from sample 5000 on."""
+    a = synth.random_walk(12000, seed=seed)
+    rng = np.random.default_rng(seed + 7)
+    b = np.concatenate([synth.random_walk(5000, seed=seed + 200), rng.standard_normal(7000)])
+    return a, b
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bias_must_be_the_running_maximum(seed):
+    m = 256
+    a, b = _drop_input(seed, m)
+    running, _ = _walk(a, b, m, k0=0, width=64, rows=8192)
+    current, _ = _walk(a, b, m, k0=0, width=64, rows=8192, bias="current")
+    assert running.max() < 1.0
+    assert current.max() > 1.5                     # after the drop the old error dominates
+    assert current[:9].max() < 1.0                 # before it the two agree
+
+
+def test_anchor_at_the_norm_drop_resets_the_error():
+    m = 256
+    a, b = _drop_input(0, m)
+    drop = 5120                                    # first chunk whose columns are all white noise
+    plain, bias_plain = _walk(a, b, m, k0=0, width=64, rows=8192)
+    anchored, bias_anch = _walk(a, b, m, k0=0, width=64, rows=8192, anchor_rows=(drop,))
+    after = slice(drop // CHUNK, None)
+    assert anchored.max() < 1.0
+    # the error-bias after the drop, in correlation units, is several times narrower
+    assert np.median(bias_plain[after] / bias_anch[after]) > 5.0
