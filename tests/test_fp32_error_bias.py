@@ -23,7 +23,9 @@ to FP32 is the fused multiply-add) against an FP64 recurrence, and check
   norms drop (random walk, then white noise), the absolute error built up
   before the drop stays, and a bias from the current chunk alone is exceeded;
 * that an anchor at the drop resets the error, so the bias there could be
-  several times narrower.
+  several times narrower;
+* the same bound, plus its worst-case term for the rounding of h and of the
+  score's two subtractions, on the non-normalised path.
 """
 import math
 
@@ -130,3 +132,52 @@ def test_anchor_at_the_norm_drop_resets_the_error():
     assert anchored.max() < 1.0
     # the error-bias after the drop, in correlation units, is several times narrower
     assert np.median(bias_plain[after] / bias_anch[after]) > 5.0
+
+
+def _walk_raw(x, m, k0, width, rows):
+    """The non-normalised path (self-join): q(i,j) = sum x_i x_j walked with
+    q += df_i dgr_j + df_j dgr_i (df = (x_{i+m-1} - x_{i-1}) / 2,
+    dgr = x_{i+m-1} + x_{i-1}) in FP32, the score (q - h_j) - h_i with
+    h = ||x_i||^2 / 2 rounded to FP32; the bias adds 4 eps (largest row h +
+    largest column h) per chunk for the rounding of h and of the two
+    subtractions.  Returns the largest |FP32 score - exact score| / E per chunk."""
+    l = len(x) - m + 1
+    win = np.lib.stride_tricks.sliding_window_view(x, m)
+    h = 0.5 * np.einsum("it,it->i", win, win)
+    df = np.zeros(l)
+    dgr = np.zeros(l)
+    df[1:] = (x[m:m + l - 1] - x[:l - 1]) / 2
+    dgr[1:] = x[m:m + l - 1] + x[:l - 1]
+    ks = k0 + np.arange(width)
+    f32 = lambda v: np.asarray(v, np.float32).astype(np.float64)
+    q64 = np.einsum("t,dt->d", win[0], win[ks])
+    q32 = q64.astype(np.float32)
+    e_c, steps = 0.0, 0
+    ratios = []
+    rms = lambda v: math.sqrt(float(np.mean(v * v)))
+    for r in range(0, rows, CHUNK):
+        R = slice(r, r + CHUNK)
+        C = slice(r + k0, r + k0 + CHUNK + width)
+        e_c = max(e_c, math.sqrt(float(np.mean(2 * h[R]))) * math.sqrt(float(np.mean(2 * h[C])))
+                  + 2 * (rms(df[R]) * rms(dgr[C]) + rms(df[C]) * rms(dgr[R])))
+        steps += CHUNK
+        E = 2.0 * EPS32 * (e_c * math.sqrt(steps + 16) + 2 * (h[R].max() + h[C].max()))
+        worst = 0.0
+        for i in range(max(r, 1), r + CHUNK):
+            j = i + ks
+            q64 = q64 + df[i] * dgr[j] + df[j] * dgr[i]
+            q32 = (q32.astype(np.float64) + f32(df[i]) * f32(dgr[j])).astype(np.float32)
+            q32 = (q32.astype(np.float64) + f32(df[j]) * f32(dgr[i])).astype(np.float32)
+            score32 = (q32 - h[j].astype(np.float32)) - np.float32(h[i])
+            exact = q64 - h[j] - h[i]
+            worst = max(worst, float(np.abs(score32.astype(np.float64) - exact).max()) / E)
+        ratios.append(worst)
+    return np.array(ratios)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_raw_bias_covers_fp32_rounding(seed):
+    x = synth.tonal(12000, seed=seed)
+    ratios = _walk_raw(x, 256, k0=128, width=64, rows=8192)
+    assert ratios.max() < 1.0
+    assert ratios.max() > 0.01
