@@ -203,14 +203,16 @@ def _ab_like(seed, m, n, block):
     return a, np.concatenate(parts)
 
 
-def _replay_groups(a, b, m, thresholds, bias=True, reanchor_drop=None, width=512, group=8,
-                   warp=256):
+def _replay_groups(a, b, m, thresholds, bias=True, reanchor_drop=None, seed_diags=0, width=512,
+                   group=8, warp=256):
     """Warp groups (8 rows x 256 diagonals) of the upper half j >= i of an AB
     join in which some cell's FP32 upper bound reaches the row's or the
     column's threshold.  thresholds: "final" (each row's and column's best
     correlation over that half) or "running" (raised by every cell as the
     bands are walked in order).  reanchor_drop: re-anchor a band when a
-    chunk's bias term falls below 1/reanchor_drop of its running maximum."""
+    chunk's bias term falls below 1/reanchor_drop of its running maximum.
+    seed_diags: running thresholds start from the exact correlations along
+    that many diagonals spread over the half (instead of -inf)."""
     winA, muA, sA, dfA, dgA = _stats(a, m)
     winB, muB, sB, dfB, dgB = _stats(b, m)
     lA, lB = len(sA), len(sB)
@@ -269,6 +271,12 @@ def _replay_groups(a, b, m, thresholds, bias=True, reanchor_drop=None, width=512
         if thresholds == "running":
             thrR[i] = max(thrR[i], rho[ok].max())
             np.maximum.at(thrC, jj[ok], rho[ok])
+    if thresholds == "running" and seed_diags:
+        for k in np.linspace(0, lB - 1, seed_diags).astype(int):
+            for i in range(min(lA, lB - k)):
+                rho = float(np.dot(winA[i] - muA[i], winB[i + k] - muB[i + k])) * iA[i] * iB[i + k]
+                thrR[i] = max(thrR[i], rho)
+                thrC[i + k] = max(thrC[i + k], rho)
     anchors[0] = 0                                 # count the extra anchors of the counting walk
     for k0 in bands:
         walk(k0, count)
@@ -290,3 +298,14 @@ def test_threshold_convergence_outweighs_the_error_bias():
     assert ideal < biased < running
     assert running - biased > biased - ideal
     assert extra > 0 and abs(anchored - biased) <= 0.05 * biased
+
+
+def test_sparse_seeds_close_little_of_the_gap():
+    """Starting the running thresholds from 16 exactly walked diagonals cuts
+    the replayed groups, but most of the gap to the final thresholds stays."""
+    a, b = _ab_like(0, 64, 3072 + 63, 512)
+    biased, _ = _replay_groups(a, b, 64, "final")
+    running, _ = _replay_groups(a, b, 64, "running")
+    seeded, _ = _replay_groups(a, b, 64, "running", seed_diags=16)
+    assert biased < seeded < running
+    assert seeded - biased > 0.5 * (running - biased)
