@@ -668,12 +668,73 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
 // groups the fast path records before their replays run
 constexpr int kQueue = 16;
 
+// The two halves of a cell's score: the part that depends on the column,
+// t = c invn_j (RAW: c - h_j), and the row's factor applied to it,
+// t invn_i (RAW: t - h_i).  The second half is non-decreasing in t (invn_i >= 0;
+// NaN for an ill-conditioned row makes every comparison false), and rounding is
+// monotone, so the largest score of a row's cells is finish(max_d t_d) exactly.
+template <bool RAW, class T>
+__device__ __forceinline__ T score_part(T c, T zc)
+{
+    if constexpr (RAW) return c - zc;
+    else return c * zc;
+}
+template <bool RAW, class T>
+__device__ __forceinline__ T score_finish(T t, T zr)
+{
+    if constexpr (RAW) return t - zr;
+    else return t * zr;
+}
+// max / min that ignore a NaN operand (a NaN score never reaches a threshold)
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+
+// The per-cell column test of one group of D rows, re-walked from the
+// group's starting covariances c0 (row stats at pr[u], column lane_off + s + v
+// at pc[v + v / D]): does any lane's cell reach its column's threshold?  Out of
+// line: it runs only for groups the fast path's group-level column test flags,
+// and keeps the fast path's registers for the hot loop.
+template <class Tr, int D, bool RAW>
+static __device__ __noinline__ bool column_recheck(const typename Tr::T *c0,
+                                                   const typename Tr::S4 *pr,
+                                                   const typename Tr::S4 *pc)
+{
+    using T = typename Tr::T;
+    using S4 = typename Tr::S4;
+    T c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = c0[d];
+    bool colhit = false;
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+        const S4 rw = pr[u];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const S4 cc = pc[(u + d) + (u + d) / D];
+            c[d] = Tr::fma_(rw.x, cc.y, c[d]);
+            c[d] = Tr::fma_(cc.x, rw.y, c[d]);
+            colhit |= (cell_score<RAW>(c[d], cc.z, rw.z) >= cc.w);
+        }
+    }
+    return __any_sync(0xffffffffu, colhit);
+}
+
 // The hot loop: rows s0 .. s1-1 of the staged chunk (whole groups of D rows)
-// for this thread's D diagonals.  Each cell costs two FMAs (the covariance
-// update), two multiplies (the correlation) and two compares (row and column
-// thresholds).  The column stats walk through a D-entry register ring; the
-// row stats are a shared-memory broadcast.  Returns the number of groups
-// recorded in q_c0 / q_s for replay.
+// for this thread's D diagonals.  It only decides which groups of D rows hold
+// a cell whose score reaches its row's or its column's threshold; those groups
+// are recorded (their starting covariances) and replayed exactly afterwards.
+// Per cell: two FMAs (the covariance update), one multiply (c invn_j) and one
+// max; per row, one multiply by invn_i and one compare give the exact row
+// test (the row's largest score against the row's threshold).  The column
+// test is first taken for the whole group at once: the group's largest score
+// against the smallest threshold of the 2D-1 columns it touches.  That can
+// only flag more groups than the per-cell test, so a group it flags (and the
+// row test did not) is re-walked from its starting covariances with the
+// per-cell column test before it is recorded.  The column stats walk through a
+// D-entry register ring; the row stats are a shared-memory broadcast.  Returns
+// the number of groups recorded in q_c0 / q_s.
 template <class Tr, int D, int RC, bool RAW>
 static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, int s1,
                                                  int lane_off, CovArr<typename Tr::T, D> *q_c0,
@@ -697,31 +758,52 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
     S4 cs[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) cs[d] = pc[d];
+    // smallest threshold of the columns in the ring (the group's first D columns)
+    T ringmin = cs[0].w;
+#pragma unroll
+    for (int d = 1; d < D; ++d) ringmin = vmin(ringmin, cs[d].w);
+    const T NINF = -Tr::inf();
     int qn = 0;
     for (int s = s0; s < s1; s += D, pc += D + 1, pr += D) {
         T c0[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) c0[d] = c[d];
-        bool hit = false;
+        bool rowhit = false;
+        T gmax = NINF;                          // the group's largest score
+        T newmin = Tr::inf();                   // columns D .. 2D-2 of the group
+        T lastw = Tr::inf();                    // column 2D-1 (the next group's ring)
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             const S4 rw = pr[u];
+            T tm = NINF;
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const S4 &cc = cs[(d + u) % D];
                 c[d] = Tr::fma_(rw.x, cc.y, c[d]);
                 c[d] = Tr::fma_(cc.x, rw.y, c[d]);
-                const T rho = cell_score<RAW>(c[d], cc.z, rw.z);
-                hit |= (rho >= rw.w);
-                hit |= (rho >= cc.w);
+                tm = vmax(tm, score_part<RAW>(c[d], cc.z));
             }
+            const T M = score_finish<RAW>(tm, rw.z);
+            rowhit |= (M >= rw.w);
+            gmax = vmax(gmax, M);
             cs[u % D] = pc[(D + 1) + u];        // column lane_off + s + u + D
+            if (u + 1 < D) newmin = vmin(newmin, cs[u % D].w);
+            else lastw = cs[u % D].w;
         }
-        if (__any_sync(0xffffffffu, hit)) {
+        const T cmin = vmin(ringmin, newmin);
+        ringmin = vmin(newmin, lastw);
+        const bool colmaybe = gmax >= cmin;
+        const bool rec = __any_sync(0xffffffffu, rowhit);
+        const bool maybe = !rec && __any_sync(0xffffffffu, colmaybe);
+        if (rec || maybe) {
+            // record the group; a group the column test only may have flagged is
+            // kept after the per-cell column test confirms it
 #pragma unroll
             for (int d = 0; d < D; ++d) q_c0[qn].v[d] = c0[d];
             q_s[qn] = s;
-            ++qn;
+            bool keep = rec;
+            if (maybe) keep = column_recheck<Tr, D, RAW>(q_c0[qn].v, pr, pc);
+            if (keep) ++qn;
         }
     }
 #pragma unroll
