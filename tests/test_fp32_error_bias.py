@@ -25,10 +25,7 @@ to FP32 is the fused multiply-add) against an FP64 recurrence, and check
 * that an anchor at the drop resets the error, so the bias there could be
   several times narrower;
 * the same bound, plus its worst-case term for the rounding of h and of the
-  score's two subtractions, on the non-normalised path;
-* on an AB-like join, that thresholds still rising send more warp groups to
-  the replay than the bias does, and that re-anchoring at norm drops does
-  not change the latter.
+  score's two subtractions, on the non-normalised path.
 """
 import math
 
@@ -184,128 +181,3 @@ def test_raw_bias_covers_fp32_rounding(seed):
     ratios = _walk_raw(x, 256, k0=128, width=64, rows=8192)
     assert ratios.max() < 1.0
     assert ratios.max() > 0.01
-
-
-def _ab_like(seed, m, n, block):
-    """rows: a random walk; columns: `block`-sample blocks, each white noise
-    or a walk continuing from the previous level (50/50)."""
-    rng = np.random.default_rng(seed)
-    a = synth.random_walk(n, seed=seed)
-    parts, level = [], 0.0
-    for b0 in range(0, n, block):
-        L = min(block, n - b0)
-        if rng.random() < 0.5:
-            seg = rng.standard_normal(L)
-        else:
-            seg = level + np.cumsum(rng.standard_normal(L))
-            level = seg[-1]
-        parts.append(seg)
-    return a, np.concatenate(parts)
-
-
-def _replay_groups(a, b, m, thresholds, bias=True, reanchor_drop=None, seed_diags=0, width=512,
-                   group=8, warp=256):
-    """Warp groups (8 rows x 256 diagonals) of the upper half j >= i of an AB
-    join in which some cell's FP32 upper bound reaches the row's or the
-    column's threshold.  thresholds: "final" (each row's and column's best
-    correlation over that half) or "running" (raised by every cell as the
-    bands are walked in order).  reanchor_drop: re-anchor a band when a
-    chunk's bias term falls below 1/reanchor_drop of its running maximum.
-    seed_diags: running thresholds start from the exact correlations along
-    that many diagonals spread over the half (instead of -inf)."""
-    winA, muA, sA, dfA, dgA = _stats(a, m)
-    winB, muB, sB, dfB, dgB = _stats(b, m)
-    lA, lB = len(sA), len(sB)
-    iA, iB = 1 / sA, 1 / sB
-    f32 = lambda v: np.asarray(v, np.float32).astype(np.float64)
-    rms = lambda v: math.sqrt(float(np.mean(v * v))) if v.size else 0.0
-
-    def exact(i, jj):
-        return np.einsum("t,dt->d", winA[i] - muA[i], winB[jj] - muB[jj][:, None])
-
-    def walk(k0, visit):
-        ks = np.arange(k0, min(k0 + width, lB))
-        rows = min(lA, lB - k0)
-        c64 = exact(0, ks)
-        c32 = c64.astype(np.float32)
-        e_c, steps = 0.0, 0
-        for r in range(0, rows, CHUNK):
-            R = slice(r, min(r + CHUNK, lA))
-            C = slice(r + k0, min(r + k0 + CHUNK + width, lB))
-            cur = rms(sA[R]) * rms(sB[C]) + 2 * (rms(dfA[R]) * rms(dgB[C]) + rms(dfB[C]) * rms(dgA[R]))
-            if reanchor_drop and r > 0 and cur * reanchor_drop < e_c:
-                anchors[0] += 1
-                c64 = exact(r - 1, np.minimum(r - 1 + ks, lB - 1))
-                c32 = c64.astype(np.float32)
-                e_c, steps = 0.0, 0
-            e_c = max(e_c, cur)
-            steps += CHUNK
-            E = 2.0 * EPS32 * e_c * math.sqrt(steps + 16) if bias else 0.0
-            for i in range(r, min(r + CHUNK, rows)):
-                j = i + ks
-                ok = j < lB
-                jj = np.minimum(j, lB - 1)
-                if i > 0:
-                    c64 = c64 + dfA[i] * dgB[jj] + dfB[jj] * dgA[i]
-                    c32 = (c32.astype(np.float64) + f32(dfA[i]) * f32(dgB[jj])).astype(np.float32)
-                    c32 = (c32.astype(np.float64) + f32(dfB[jj]) * f32(dgA[i])).astype(np.float32)
-                visit(i, r, jj, ok, c64 * iA[i] * iB[jj], (c32.astype(np.float64) + E) * iA[i] * iB[jj])
-
-    bands = range(0, lB, width)
-    anchors = [0]
-    thrR = np.full(lA, -np.inf)
-    thrC = np.full(lB, -np.inf)
-    if thresholds == "final":
-        def best(i, r, jj, ok, rho, up):
-            thrR[i] = max(thrR[i], rho[ok].max())
-            np.maximum.at(thrC, jj[ok], rho[ok])
-        for k0 in bands:
-            walk(k0, best)
-    hits = set()
-
-    def count(i, r, jj, ok, rho, up):
-        trig = ok & ((up >= thrR[i]) | (up >= thrC[jj]))
-        for w in range(0, len(trig), warp):
-            if trig[w:w + warp].any():
-                hits.add((int(jj[0]) - i, r, (i - r) // group, w))
-        if thresholds == "running":
-            thrR[i] = max(thrR[i], rho[ok].max())
-            np.maximum.at(thrC, jj[ok], rho[ok])
-    if thresholds == "running" and seed_diags:
-        for k in np.linspace(0, lB - 1, seed_diags).astype(int):
-            for i in range(min(lA, lB - k)):
-                rho = float(np.dot(winA[i] - muA[i], winB[i + k] - muB[i + k])) * iA[i] * iB[i + k]
-                thrR[i] = max(thrR[i], rho)
-                thrC[i + k] = max(thrC[i + k], rho)
-    anchors[0] = 0                                 # count the extra anchors of the counting walk
-    for k0 in bands:
-        walk(k0, count)
-    return len(hits), anchors[0]
-
-
-REANCHOR_DROP = 1.5          # re-anchor when a chunk's bias term falls below 1/1.5 of the maximum
-
-
-def test_threshold_convergence_outweighs_the_error_bias():
-    """On an AB-like join the groups sent to the replay by thresholds that are
-    still rising outnumber those the error bias adds at the final
-    thresholds, and re-anchoring at norm drops barely changes the latter."""
-    a, b = _ab_like(0, 64, 3072 + 63, 512)
-    ideal, _ = _replay_groups(a, b, 64, "final", bias=False)
-    biased, _ = _replay_groups(a, b, 64, "final")
-    anchored, extra = _replay_groups(a, b, 64, "final", reanchor_drop=REANCHOR_DROP)
-    running, _ = _replay_groups(a, b, 64, "running")
-    assert ideal < biased < running
-    assert running - biased > biased - ideal
-    assert extra > 0 and abs(anchored - biased) <= 0.05 * biased
-
-
-def test_sparse_seeds_close_little_of_the_gap():
-    """Starting the running thresholds from 16 exactly walked diagonals cuts
-    the replayed groups, but most of the gap to the final thresholds stays."""
-    a, b = _ab_like(0, 64, 3072 + 63, 512)
-    biased, _ = _replay_groups(a, b, 64, "final")
-    running, _ = _replay_groups(a, b, 64, "running")
-    seeded, _ = _replay_groups(a, b, 64, "running", seed_diags=16)
-    assert biased < seeded < running
-    assert seeded - biased > 0.5 * (running - biased)
