@@ -218,18 +218,33 @@ mp_status mp_fluss(const int64_t *pi, int64_t l, int64_t edge, int32_t num_segme
  * is a convenience of the library).  For callers that cannot allocate device
  * memory -- code running inside another framework's CUDA-graph capture, under
  * an allocator that owns all device memory, or in a plugin that only receives
- * its input and output buffers.  Same arguments and results as mp_selfjoin,
- * but the scratch is a 64 MiB array the library keeps on every GPU that
- * loads it, until the process exits; it holds any series of up to 930,000
- * samples (larger n returns MP_ENOMEM; nothing is allocated by any call).
- * The first call on a device (with that device current) looks up the
- * array's device address, so make it before any stream capture.  All calls
- * on a device share the array: calls whose GPU work may overlap race and
- * must be serialised by the caller.  Device-side status (non-finite input)
- * is not readable for this entry point; check the input beforehand.
+ * its input and output buffers.  Same arguments and results as mp_selfjoin
+ * (the same neighbours and distances, bit for bit, for the same cfg), but the
+ * scratch is a 64 MiB array the library keeps on every GPU that loads it,
+ * until the process exits; nothing is allocated by any call.
+ * Size limit: the series' mp_selfjoin workspace must fit in the 64 MiB, about
+ * 97 bytes per sample with the FP32-mixed precision and 81 with FP64 (plus the
+ * tile plan): n up to 690,064 (FP32-mixed) or 826,400 (FP64) with the
+ * default tile shapes; mp_selfjoin_noalloc_max_n(cfg) returns the exact
+ * largest n for a configuration (0 for an invalid one).  A larger n returns MP_ENOMEM before
+ * any work is enqueued.
+ * Each call looks up the array's device address in the current device's
+ * context (an address kept from an earlier call would be stale after
+ * cudaDeviceReset or in another context); the first call on a device also
+ * loads the library's device code there, so make it before any stream
+ * capture.  All calls on a device share the array, which keeps the last call's
+ * contents (every call clears what must start at zero): calls whose GPU work
+ * may overlap race and must be serialised by the caller.
+ * Device-side errors (non-finite input, MP_EINVAL_DATA; a bounded retry loop
+ * that gave up, MP_ETIMEOUT) land in the array's status word:
+ * mp_selfjoin_noalloc_device_status(stream) synchronises `stream`, reads and
+ * clears it, like mp_get_device_status does for a caller workspace (the same
+ * race caveat applies).
  */
+int64_t mp_selfjoin_noalloc_max_n(const mp_config *cfg);
 mp_status mp_selfjoin_noalloc(const void *x, int32_t dtype, int64_t n, const mp_config *cfg,
                               double *mp, int64_t *pi, void *stream);
+mp_status mp_selfjoin_noalloc_device_status(void *stream);
 
 /*
  * AB-join (Sec. 3.2, two series; no exclusion zone).  For every window of a:

@@ -66,6 +66,8 @@ SIGNATURES = {
     "mp_fluss": (ctypes.c_int, [_vp, _i64, _i64, _i32, _i64, _vp, _vp, _vp, _sz, _vp]),
     "mp_selfjoin_lr": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mp_selfjoin_noalloc": (ctypes.c_int, [_vp, _i32, _i64, _cfgp, _vp, _vp, _vp]),
+    "mp_selfjoin_noalloc_max_n": (_i64, [_cfgp]),
+    "mp_selfjoin_noalloc_device_status": (ctypes.c_int, [_vp]),
     "mp_abjoin_workspace_bytes": (_sz, [_i64, _i64, _cfgp]),
     "mp_abjoin": (ctypes.c_int, [_vp, _i64, _vp, _i64, _i32, _cfgp, _vp, _vp, _vp, _vp, _vp, _sz,
                                  _vp]),

@@ -9,46 +9,52 @@
 // itself owns: one file-scope device array of kNoAllocScratchBytes (64 MiB),
 // which every GPU that loads the library keeps until the process exits.
 //
-// The array's name is only a host-side stand-in in host code, so the first
-// call on each device (with that device current) looks up its device address
-// with cudaGetSymbolAddress and caches it; that first call should therefore
-// come before any stream capture.  All calls on a device share the one array
-// and it keeps whatever the last call left in it; the join clears what must
-// start at zero (its header and keys) itself.  Calls whose work overlaps on
-// the GPU (different streams, or host threads, without ordering between
-// them) race on the array and give wrong results: serialise them.
-#include <mutex>
-
+// The array's name is only a host-side stand-in in host code: its device
+// address belongs to the CUDA context the library's device code is loaded
+// in.  Every call therefore looks the address up with cudaGetSymbolAddress,
+// on the device current at the call, instead of keeping one from an earlier
+// call (a cached address would go stale after cudaDeviceReset or in another
+// context).  The first call on a device also loads the library's device code
+// there, so make that first call before any stream capture.  All calls on a
+// device share the one array and it keeps whatever the last call left in it;
+// the join clears what must start at zero (its header and keys) itself.
+// Calls whose work overlaps on the GPU (different streams, or host threads,
+// without ordering between them) race on the array and give wrong results:
+// serialise them.
 #include "internal.cuh"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-void *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
-std::mutex g_noalloc_mu;
-
-// device address of the scratch array on the current device (set up once)
+// device address of the scratch array in the current device's context
 mp_status noalloc_scratch(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return MP_ECUDA;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return MP_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
-            return MP_ECUDA;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+        return MP_ECUDA;
+    *out = p;
     return MP_OK;
 }
 
 }  // namespace
+
+extern "C" int64_t mp_selfjoin_noalloc_max_n(const mp_config *cfg)
+{
+    if (!cfg || cfg->m < 4) return 0;
+    // the workspace grows with n: the largest n whose workspace fits
+    int64_t lo = cfg->m, hi = (int64_t)1 << 31;
+    const size_t first = mp_selfjoin_workspace_bytes(lo, cfg);
+    if (first == 0 || first > kNoAllocScratchBytes) return 0;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        const size_t need = mp_selfjoin_workspace_bytes(mid, cfg);
+        if (need != 0 && need <= kNoAllocScratchBytes) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 extern "C" mp_status mp_selfjoin_noalloc(const void *x, int32_t dtype, int64_t n,
                                          const mp_config *cfg, double *mp, int64_t *pi,
@@ -62,4 +68,12 @@ extern "C" mp_status mp_selfjoin_noalloc(const void *x, int32_t dtype, int64_t n
     const mp_status s = noalloc_scratch(&ws);
     if (s != MP_OK) return s;
     return mp_selfjoin(x, dtype, n, cfg, mp, pi, ws, kNoAllocScratchBytes, stream);
+}
+
+extern "C" mp_status mp_selfjoin_noalloc_device_status(void *stream)
+{
+    void *ws = nullptr;
+    const mp_status s = noalloc_scratch(&ws);
+    if (s != MP_OK) return s;
+    return mp_get_device_status(ws, stream);
 }
