@@ -304,7 +304,8 @@ def run_ours(args, world, rank, local):
     x = torch.from_numpy(x_np).cuda()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     import ctypes
-    cfg = _lib.make_config(m, 0.5, args.prec, flags=_lib.MP_FLAG_RAW if raw else 0)
+    tilekw = {"variant": args.variant, "tile_rows": args.tile_rows, "anchor_every": args.anchor_every}
+    cfg = _lib.make_config(m, 0.5, args.prec, flags=_lib.MP_FLAG_RAW if raw else 0, **tilekw)
     lr = args.join == "lr"
     anytime = args.join == "anytime"
     need = (lib.mp_selfjoin_lr_workspace_bytes if lr else lib.mp_selfjoin_workspace_bytes)(
@@ -320,7 +321,7 @@ def run_ours(args, world, rank, local):
             run = api.Anytime(xx, m, seed=1, prec=prec, ws=ws)
             run.run(0.05)
             return run.run(1.0)
-        return api.selfjoin(xx, m, 0.5, prec, raw=raw, ws=ws)
+        return api.selfjoin(xx, m, 0.5, prec, raw=raw, ws=ws, **(tilekw if prec == args.prec else {}))
 
     def step(prec):
         return join(x, prec)
@@ -412,6 +413,25 @@ def run_ours(args, world, rank, local):
     e2e_total = max_over_ranks(sum(e2e_ms), world)
     e2e_value = world * cells * args.steps / (e2e_total / 1e3) / 1e9
 
+    # the other join families at their parity-test sizes, library-default tiles
+    # (batched and pan also as CUDA-graph replays), and the differentiable step
+    families = None
+    if args.families and not (lr or anytime or raw) and world == 1:
+        families = {}
+        peaks0 = measured_peaks()
+        issue_peak0 = (torch.cuda.get_device_properties(0).multi_processor_count * 128 *
+                       float(peaks0.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12)
+        fsteps = max(3, min(args.steps, 3))
+        with ClockSampler(local) as fclk:
+            for fj in ("ab", "batched", "pan"):
+                case = family_case(fj)
+                res = time_family(case, {}, fsteps, 3, flush, graph=fj in ("batched", "pan"))
+                families[fj] = family_summary(fj, case, res, {"tuned": False}, issue_peak0, world)
+                del res
+            families["grad"] = measure_grad(fsteps, 3, flush, issue_peak0)
+        families["clocks"] = fclk.summary()
+        families["steps"] = fsteps
+
     if rank != 0:
         return
     props = torch.cuda.get_device_properties(0)
@@ -446,6 +466,8 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if families is not None:
+        line["families"] = families
     if not args.skip_cpu and world == 1:
         rate, rows, secs, cores, results = cpu_oracle_rate(x_np, m, E, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gcells/s", "cores": cores,
@@ -546,6 +568,50 @@ def run_fluss(args, world, rank, local):
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_grad(steps, warmup, flush, issue_peak):
+    """The differentiable step of the 2^16 walk (m = 128): FP32-mixed forward,
+    loss = sum(MP) + mean of the 16 largest, backward scatter; eager steps,
+    L2 flushed before each.  Returns the default run's summary object."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, synth
+    lib = _lib.load()
+    n, m = 1 << 16, 128
+    cells = selfjoin_cells(n - m + 1, math.ceil(0.5 * m))
+    x = torch.from_numpy(synth.random_walk(n, seed=58, dtype=np.float32)).cuda().requires_grad_(True)
+    kms = ctypes.c_float()
+
+    def step():
+        x.grad = None
+        prof, _ = api.matrix_profile(x, m)
+        loss = prof.sum() + prof.topk(16).values.mean()
+        loss.backward()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times, kern = [], []
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        step()
+        e.record()
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+        _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+        kern.append(kms.value)
+    ms = statistics.mean(times)
+    kernel_ms = statistics.mean(kern)
+    return {"workload": f"random walk n={n} float32, m={m}, loss = sum(MP) + mean(top-16 MP), "
+                        "forward + backward", "cells": cells, "ms_per_step": ms,
+            "value": cells / (ms / 1e3) / 1e9, "unit": "Gcells/s", "kernel_ms": kernel_ms,
+            "roofline_frac": 6 * cells / (kernel_ms / 1e3) / 1e12 / issue_peak}
 
 
 def run_grad(args, world, rank, local):
@@ -673,37 +739,27 @@ def run_grad(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_family(args, world, rank, local):
-    """--join ab | batched | pan: the other join families at their parity-test
-    sizes (AB: a 2^21 walk against a 2^19 walk / white-noise mix with flat
-    stretches, m = 512; batched: 4096 ragged walks of 1000..65536 samples,
-    m in {32, 64, 128}; pan: a 2^16 walk over 64 window sizes 16..1024),
-    FP32-mixed, L2 flushed between steps, timed like the self-join.  The
-    autotuner first chooses the tile configuration on the same input
-    (untimed; --no-tune keeps the library's defaults)."""
-    import ctypes
-
+def family_case(join: str):
+    """Inputs and call of one join family at its parity-test size (AB: a 2^21
+    walk against a 2^19 walk / white-noise mix with flat stretches, m = 512;
+    batched: 4096 ragged walks of 1000..65536 samples, m in {32, 64, 128};
+    pan: a 2^16 walk over 64 window sizes 16..1024).  Returns a dict with the
+    host inputs, the admissible cells, a description, call(dev_inputs, kw) ->
+    outputs, the output bytes, and the tuner entry point."""
     import torch
 
-    from paper_1904_12626_gb300 import _lib, api, build, synth
-    build.build()
-    api.init()
-    lib = _lib.load()
-    _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    kw: dict = {}                   # tile configuration (the library's defaults with --no-tune)
-    if args.join == "ab":
+    from paper_1904_12626_gb300 import api, synth
+    if join == "ab":
         m = 512
         a_np = synth.random_walk(1 << 21, seed=51, dtype=np.float32)
         b_np, _ = synth.mixed_with_flats(1 << 19, m, seed=52)
         la, lb = len(a_np) - m + 1, len(b_np) - m + 1
-        cells = la * lb
-        inputs = [a_np, b_np]
-        desc = f"AB-join, 2^21 random walk x 2^19 walk/white-noise mix with flat stretches, m={m}"
-        def call(xs):
-            return api.abjoin(xs[0], xs[1], m, "fp32", **kw)
-        out_bytes = 16 * (la + lb)
-    elif args.join == "batched":
+        return {"inputs": [a_np, b_np], "cells": la * lb, "out_bytes": 16 * (la + lb),
+                "desc": f"AB-join, 2^21 random walk x 2^19 walk/white-noise mix with flat "
+                        f"stretches, m={m}",
+                "call": lambda xs, kw: api.abjoin(xs[0], xs[1], m, "fp32", **kw),
+                "tune": lambda tuner, xs: tuner.abjoin(xs[0], xs[1], m)}
+    if join == "batched":
         values, offsets, ms = synth.ragged_batch(4096, seed=55)
         cells = 0
         for b in range(len(ms)):
@@ -711,67 +767,137 @@ def run_family(args, world, rank, local):
             cells += selfjoin_cells(l_b, math.ceil(0.5 * int(ms[b])))
         o_t = torch.from_numpy(offsets).cuda()
         m_t = torch.from_numpy(ms).cuda()
-        inputs = [values]
         max_m = int(ms.max())
-        desc = "batched self-joins, 4096 random walks of 1000..65536 samples, m in {32,64,128}"
-        def call(xs):
+
+        def call(xs, kw):
             mp, pi, _ = api.batched(xs[0], o_t, m_t, max_m=max_m, **kw)
             return mp, pi
-        out_bytes = 16 * len(values)
-    else:
-        n = 1 << 16
-        ms = synth.pan_windows()
-        x_np = synth.random_walk(n, seed=57, dtype=np.float32)
-        cells = sum(selfjoin_cells(n - int(mk) + 1, math.ceil(0.5 * int(mk))) for mk in ms)
-        inputs = [x_np]
-        desc = "pan profile, 2^16 random walk, 64 window sizes 16..1024"
-        def call(xs):
-            return api.pan(xs[0], ms, **kw)
-        out_bytes = 16 * len(ms) * (n - int(ms.min()) + 1)
-    dev_in = [torch.from_numpy(v).cuda() for v in inputs]
-    tile = {"tuned": False}
-    if args.tune:                   # untimed: the autotuner chooses the tile configuration
-        from paper_1904_12626_gb300.tune import Tuner
-        tuner = Tuner(args.tune_cache or None, warmup=0, reps=1)   # the check run warms up
-        if args.join == "ab":
-            kw.update(tuner.abjoin(dev_in[0], dev_in[1], m))
-        elif args.join == "batched":
-            kw.update(tuner.batched(dev_in[0], o_t, m_t, max_m=max_m))
-        else:
-            kw.update(tuner.pan(dev_in[0], ms))
-        ch = tuner.last
-        tile = {"tuned": True, **kw, "tuner_default_ms": ch.default_ms, "tuner_ms": ch.ms,
-                "candidates_timed": ch.measured}
-    for _ in range(args.warmup):
-        call(dev_in)
+        return {"inputs": [values], "cells": cells, "out_bytes": 16 * len(values),
+                "desc": "batched self-joins, 4096 random walks of 1000..65536 samples, "
+                        "m in {32,64,128}",
+                "call": call,
+                "tune": lambda tuner, xs: tuner.batched(xs[0], o_t, m_t, max_m=max_m)}
+    n = 1 << 16
+    ms = synth.pan_windows()
+    x_np = synth.random_walk(n, seed=57, dtype=np.float32)
+    cells = sum(selfjoin_cells(n - int(mk) + 1, math.ceil(0.5 * int(mk))) for mk in ms)
+    return {"inputs": [x_np], "cells": cells, "out_bytes": 16 * len(ms) * (n - int(ms.min()) + 1),
+            "desc": "pan profile, 2^16 random walk, 64 window sizes 16..1024",
+            "call": lambda xs, kw: api.pan(xs[0], ms, **kw),
+            "tune": lambda tuner, xs: tuner.pan(xs[0], ms)}
+
+
+def time_family(case, kw, steps, warmup, flush, graph):
+    """Eager steps (whole call, and the tile kernel alone), then, with `graph`,
+    the same call recorded once in a CUDA graph and replayed per step; L2
+    flushed before every timed step."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib
+    lib = _lib.load()
+    dev_in = [torch.from_numpy(v).cuda() for v in case["inputs"]]
+    call = case["call"]
+    for _ in range(warmup):
+        call(dev_in, kw)
     torch.cuda.synchronize()
     kms = ctypes.c_float()
     times, kern = [], []
-    barrier(world)
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        call(dev_in, kw)
+        e.record()
+        e.synchronize()
+        times.append(s.elapsed_time(e))
+        _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
+        kern.append(kms.value)
+    out = {"times": times, "kernel_ms": statistics.mean(kern), "dev_in": dev_in}
+    if graph:
+        _lib.check(lib.mp_timing_enable(0), "mp_timing_enable")   # no host events in a capture
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            call(dev_in, kw)
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        gt = []
+        for _ in range(steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record()
-            call(dev_in)
+            g.replay()
             e.record()
             e.synchronize()
-            times.append(s.elapsed_time(e))
-            _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
-            kern.append(kms.value)
+            gt.append(s.elapsed_time(e))
+        del g
+        _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
+        out["graph_times"] = gt
+    return out
+
+
+def family_summary(join, case, res, tile, issue_peak, world):
+    """The per-family object of the bench line (eager and graph-replay times,
+    the tile kernel against the issue roofline)."""
+    ms = statistics.mean(res["times"])
+    d = {"workload": case["desc"], "cells": case["cells"], "ms_per_step": ms,
+         "value": case["cells"] / (ms / 1e3) / 1e9, "unit": "Gcells/s",
+         "kernel_ms": res["kernel_ms"],
+         "roofline_frac": 6 * case["cells"] / (res["kernel_ms"] / 1e3) / 1e12 / issue_peak,
+         "tile": tile}
+    if "graph_times" in res:
+        gms = statistics.mean(res["graph_times"])
+        d["graph_ms_per_step"] = gms
+        d["graph_value"] = case["cells"] / (gms / 1e3) / 1e9
+    return d
+
+
+def run_family(args, world, rank, local):
+    """--join ab | batched | pan: the other join families at their parity-test
+    sizes, FP32-mixed, L2 flushed between steps, timed like the self-join
+    (batched and pan also as CUDA-graph replays).  The autotuner first
+    chooses the tile configuration on the same input (untimed; --no-tune keeps
+    the library's defaults)."""
+    import ctypes
+
+    import torch
+
+    from paper_1904_12626_gb300 import _lib, api, build
+    build.build()
+    api.init()
+    lib = _lib.load()
+    _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    case = family_case(args.join)
+    kw: dict = {}                   # tile configuration (the library's defaults with --no-tune)
+    tile = {"tuned": False}
+    if args.tune:                   # untimed: the autotuner chooses the tile configuration
+        from paper_1904_12626_gb300.tune import Tuner
+        tuner = Tuner(args.tune_cache or None, warmup=0, reps=1)   # the check run warms up
+        kw.update(case["tune"](tuner, [torch.from_numpy(v).cuda() for v in case["inputs"]]))
+        ch = tuner.last
+        tile = {"tuned": True, **kw, "tuner_default_ms": ch.default_ms, "tuner_ms": ch.ms,
+                "candidates_timed": ch.measured}
     barrier(world)
-    total_ms = max_over_ranks(sum(times), world)
-    kernel_ms = max_over_ranks(statistics.mean(kern), world)
-    host_in = [torch.from_numpy(v).pin_memory() for v in inputs]
+    with ClockSampler(local) as clk:
+        res = time_family(case, kw, args.steps, args.warmup, flush,
+                          graph=args.join in ("batched", "pan"))
+    barrier(world)
+    total_ms = max_over_ranks(sum(res["times"]), world)
+    kernel_ms = max_over_ranks(res["kernel_ms"], world)
+    host_in = [torch.from_numpy(v).pin_memory() for v in case["inputs"]]
     e2e = []
     for it in range(args.warmup + args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
-        res = call([h.to("cuda", non_blocking=True) for h in host_in])
-        _ = [r.to("cpu", non_blocking=True) for r in res if r is not None]
+        out = case["call"]([h.to("cuda", non_blocking=True) for h in host_in], kw)
+        _ = [r.to("cpu", non_blocking=True) for r in out if r is not None]
         e.record()
         e.synchronize()
         if it >= args.warmup:
@@ -783,24 +909,29 @@ def run_family(args, world, rank, local):
     f_max = float(peaks.get("sm_max_mhz") or 2070.0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     issue_peak = sms * 128 * f_max * 1e6 / 1e12
+    cells = case["cells"]
     achieved = 6 * cells / (kernel_ms / 1e3) / 1e12
+    fam = family_summary(args.join, case, res, tile, issue_peak, world)
     line = {
         "metric": f"{args.join} Gcells/s (FP32-mixed)",
         "value": replica_value(world, cells, args.steps, total_ms), "unit": "Gcells/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)", "data": "synthetic",
-        "config": {"workload": desc, "cells": cells, "tile": tile,
+        "config": {"workload": case["desc"], "cells": cells, "tile": tile,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
                      "frac": achieved / issue_peak, "traffic": None, "kernel_ms": kernel_ms},
         "e2e": {"value": replica_value(world, cells, args.steps, e2e_total), "unit": "Gcells/s",
-                "h2d_bytes_per_step": int(sum(v.nbytes for v in inputs)),
-                "d2h_bytes_per_step": int(out_bytes)},
+                "h2d_bytes_per_step": int(sum(v.nbytes for v in case["inputs"])),
+                "d2h_bytes_per_step": int(case["out_bytes"])},
         "gpu_launches": 11 * args.steps,
         "clocks": clk.summary(),
     }
+    if "graph_ms_per_step" in fam:
+        line["graph_ms_per_step"] = fam["graph_ms_per_step"]
+        line["graph_value"] = fam["graph_value"]
     print(json.dumps(line), flush=True)
 
 
@@ -822,6 +953,12 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=12.0)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="self-join tile variant (mp_variant_info; 0: the library default)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="self-join row-tile height (0: library's)")
+    ap.add_argument("--anchor-every", type=int, default=0, help="self-join re-anchor interval (0: none)")
+    ap.add_argument("--no-families", dest="families", action="store_false",
+                    help="default run: skip the AB / batched / pan / gradient measurements")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="--join ab | batched | pan: keep the library's default tile configuration "
                          "(by default the autotuner chooses it first, untimed)")
