@@ -40,14 +40,20 @@ def _stale(obj: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out_dir: str | None = None) -> str:
+    """Build the library; returns its path.  `extra_flags` go to every nvcc
+    compile (e.g. -D overrides of the device loop limits); with `out_dir` the
+    objects and the library go there instead of the package (a variant build
+    that leaves the package's own library alone)."""
+    obj_dir = os.path.join(out_dir, "obj") if out_dir else OUT
+    lib_path = os.path.join(out_dir, "libmpgb.so") if out_dir else LIB
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "mp.h")]
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s, *headers, __file__]):
             cmd = [nvcc(), *_flags(extra_flags), "-c", s, "-o", o]
@@ -69,14 +75,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     failed.append(cmd[-3])
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(failed))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -54,7 +54,7 @@ __device__ void merge_exact_f32(Key128 *key, float e, long long idx, long long o
     c.idx = idx;
     float kx = 0.0f;
     long long kx_idx = -1;
-    for (int round = 0; round < 64; ++round) {
+    for (int round = 0; round < kMergeRounds; ++round) {
         const Key128 cur = key_peek(key);
         const int dec = classify(c, cur, kx, kx_idx);
         if (dec == kDiscard) return;

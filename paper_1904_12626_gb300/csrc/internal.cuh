@@ -29,7 +29,21 @@ constexpr int kMaxSlots = 16;
 constexpr int kPad = kMaxTileDiags + kMaxSlots + 16;
 
 constexpr int kWindowsPerThread = 32;     // stats kernel: windows per thread run
-constexpr unsigned kCasRetryLimit = 1u << 20;
+// Bounded device loops: a 128-bit compare-and-swap is retried at most
+// kCasRetryLimit times, and a candidate merge takes at most kMergeRounds
+// rounds (each round settles every decision that needs no exact value, and
+// computes the exact values the next round needs); a loop that runs out
+// records MP_ETIMEOUT in the workspace status word and returns.  Both can be
+// lowered at compile time (-DMPGB_CAS_RETRY_LIMIT=..., -DMPGB_MERGE_ROUNDS=...)
+// so that a test can make them run out.
+#ifndef MPGB_CAS_RETRY_LIMIT
+#define MPGB_CAS_RETRY_LIMIT (1u << 20)
+#endif
+#ifndef MPGB_MERGE_ROUNDS
+#define MPGB_MERGE_ROUNDS 64
+#endif
+constexpr unsigned kCasRetryLimit = MPGB_CAS_RETRY_LIMIT;
+constexpr int kMergeRounds = MPGB_MERGE_ROUNDS;
 
 // four doubles, 32-byte aligned (two 16-byte vector loads)
 struct alignas(32) D4 {

@@ -356,7 +356,7 @@ static __device__ __noinline__ void warp_merge(const Prob &P, bool pending, Cand
 {
     float kx = 0.0f;
     long long kx_idx = -1;
-    for (int round = 0; round < 64; ++round) {
+    for (int round = 0; round < kMergeRounds; ++round) {
         bool need_c = false, need_k = false;
         long long kpair = -1;
         if (pending) {
@@ -762,20 +762,19 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
     T ringmin = cs[0].w;
 #pragma unroll
     for (int d = 1; d < D; ++d) ringmin = vmin(ringmin, cs[d].w);
-    const T NINF = -Tr::inf();
     int qn = 0;
     for (int s = s0; s < s1; s += D, pc += D + 1, pr += D) {
         T c0[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) c0[d] = c[d];
         bool rowhit = false;
-        T gmax = NINF;                          // the group's largest score
+        T gmax = -Tr::inf();                    // the group's largest score
         T newmin = Tr::inf();                   // columns D .. 2D-2 of the group
         T lastw = Tr::inf();                    // column 2D-1 (the next group's ring)
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             const S4 rw = pr[u];
-            T tm = NINF;
+            T tm = -Tr::inf();
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const S4 &cc = cs[(d + u) % D];
