@@ -7,6 +7,7 @@ import pytest
 import oracle
 from paper_1904_12626_gb300 import synth
 
+import _golden
 from _parity import check_rows
 
 torch = pytest.importorskip("torch")
@@ -99,28 +100,31 @@ def test_edge_cases(mp, prec):
     assert np.all(g_mp <= 1e-6) and np.array_equal(g_pi, np.arange(len(g_pi)))
 
 
+@pytest.fixture(scope="module")
+def planted():
+    """The planted 2^20 walk and the oracle's answers on its sampled rows
+    (4,096 seeded rows plus every planted row +-4)."""
+    x, info, m = _golden.c2_inputs()
+    answers, _ = _golden.c2_oracle(x, info, m)
+    return x, info, m, answers
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_planted_full_size_sampled(mp, prec):
+def test_planted_full_size_sampled(mp, planted, prec):
     """n = 2^20 float32 random walk with 3 planted motif pairs and a planted
     discord, m = 256, in the launch configuration the benchmark times; the
-    oracle checks a seeded sample of rows plus every planted row."""
-    n, m = 1 << 20, 256
-    x, info = synth.planted_walk(n, m, seed=2024)
+    oracle checks 4,096 seeded rows plus every planted row +-4."""
+    x, info, m, (rows, mp_o, pi_o, sec_o) = planted
+    assert len(rows) >= 4096 + 60
     g_mp, g_pi = _run(mp, x, m, prec=prec)
-    l = n - m + 1
-    planted = []
-    for p1, p2 in info["pairs"]:
-        for p in (p1, p2):
-            planted += list(range(p - 4, p + 5))
-    d = info["discord"]
-    planted += list(range(d - 4, d + 5))
-    rows = np.unique(np.concatenate([synth.sample_rows(l, 160, seed=7), planted]))
     x64 = x.astype(np.float64)
-    mp_o, pi_o, sec_o = oracle.selfjoin(x64, m, rows=rows)
     check_rows(x64, m, rows, g_mp, g_pi, mp_o, pi_o, sec_o, TOL[prec], excl=128)
+    planted_rows = _golden.c2_planted_rows(info)
+    assert np.isin(planted_rows, rows).all()
     for p1, p2 in info["pairs"]:
         assert abs(g_pi[p1] - p2) <= 2 and abs(g_pi[p2] - p1) <= 2
     top = int(np.argmax(g_mp))
+    d = info["discord"]
     assert d - m + 1 <= top <= d + m - 1
 
 
