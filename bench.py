@@ -265,6 +265,38 @@ def config_block(args, E, cells):
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
+def workspace_tiles(ws) -> int:
+    """Tiles the last join on workspace `ws` planned (the workspace header's
+    tile count, bytes 24..31)."""
+    return int(ws[24:32].cpu().numpy().view(np.uint64)[0])
+
+
+def fp64_roofline(cells, kernel_ms, anchor_fma, torch):
+    """The all-FP64 tile kernel against the FP64 pipe, whose rate the library's
+    probe measures on this GPU (mp_probe_fp64_rate: DFMA from independent
+    chains).  Per cell 2 DFMA (the recurrence) + 1 DMUL (c invn_j), per row of
+    8 cells one more DMUL (invn_i): 3.125 FP64 arithmetic ops; the anchors add
+    m DFMA per diagonal per tile."""
+    import ctypes
+
+    from paper_1904_12626_gb300 import _lib
+    rate = ctypes.c_double()
+    _lib.check(_lib.load().mp_probe_fp64_rate(ctypes.byref(rate)), "mp_probe_fp64_rate")
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = rate.value / 1e12                                        # T FP64 lane-ops/s
+    ops = 3.125 * cells + anchor_fma
+    achieved = ops / (kernel_ms / 1e3) / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": peak,
+            "unit": "T FP64 lane-ops/s (3.125 per cell: 2 DFMA, 1 + 1/8 DMUL; plus anchors)",
+            "frac": achieved / peak, "anchor_dfma": anchor_fma,
+            "anchor_share_of_ops": anchor_fma / ops,
+            "peak_basis": (f"measured by mp_probe_fp64_rate on this GPU: "
+                           f"{rate.value / (sms * f_max * 1e6):.2f} DFMA lanes/clk/SM at "
+                           f"{f_max:.0f} MHz x {sms} SMs")}
+
+
 def traffic_from_profile():
     """dram bytes (read + write) per tile-kernel launch, or None when the kernel
     sources changed since the capture."""
@@ -364,6 +396,7 @@ def run_ours(args, world, rank, local):
     api.device_status(ws)
     total_ms = max_over_ranks(sum(step_ms), world)
     kernel_ms = max_over_ranks(statistics.mean(kern_ms), world)
+    tiles32 = workspace_tiles(ws)
     if anytime:                # the tile kernel runs twice per step: rate the whole step
         kernel_ms = total_ms / args.steps
     value = replica_value(world, cells, args.steps, total_ms)
@@ -387,9 +420,15 @@ def run_ours(args, world, rank, local):
             t64.append(s.elapsed_time(e))
         _lib.check(lib.mp_timing_last_ms(ctypes.byref(kms)), "timing")
         ms64 = max_over_ranks(statistics.mean(t64), world)
+        kern64 = kms.value
         fp64 = {"value": cells / (ms64 / 1e3) / 1e9, "unit": "Gcells/s", "ms_per_step": ms64,
-                "kernel_ms": kms.value}
+                "kernel_ms": kern64}
         out64 = [t.cpu().numpy() for t in api.selfjoin(x, m, 0.5, "fp64", ws=ws64)]
+        torch.cuda.synchronize()
+        tiles64 = workspace_tiles(ws64)
+        td64 = ctypes.c_int32()
+        _lib.check(lib.mp_variant_info(0, 0, ctypes.byref(td64), ctypes.byref(rc)), "mp_variant_info")
+        fp64["roofline"] = fp64_roofline(cells, kern64, tiles64 * td64.value * m, torch)
         del ws64
 
     # end to end through the public API: pinned host input in, MP/PI back to host
@@ -458,7 +497,12 @@ def run_ours(args, world, rank, local):
                                    f"({'measured max clock' if peaks else 'nominal max clock'})",
                      "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),
                      "frac_at_median_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
-                                              if clocks.get("sm_mhz") else None)},
+                                              if clocks.get("sm_mhz") else None),
+                     "anchors": {"tiles": tiles32, "terms": tiles32 * td.value * m,
+                                 "fp32_lane_ops": 12 * tiles32 * td.value * m,
+                                 "fp32_lane_ops_per_cell": 12 * tiles32 * td.value * m / cells,
+                                 "note": "compensated FP32 dot products (Dot2, 12 FP32 ops per "
+                                         "term) at each tile's first row, m terms per diagonal"}},
         "fp64": fp64,
         "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": {"value": e2e_value, "unit": "Gcells/s", "h2d_bytes_per_step": 4 * n,

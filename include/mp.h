@@ -314,6 +314,15 @@ mp_status mp_timing_enable(int32_t on);
 mp_status mp_timing_last_ms(float *ms);
 
 /*
+ * Diagnostics: the FP64 pipe's throughput on the current device, in FP64
+ * lane-operations per second (fused multiply-adds from eight independent
+ * chains per thread, 32 warps per SM, three timed launches after a warm-up;
+ * synchronises the device).  The all-FP64 kernel's roofline is reported
+ * against it.  Allocates nothing.
+ */
+mp_status mp_probe_fp64_rate(double *lane_ops_per_s);
+
+/*
  * Synchronise `stream`, read the status word of workspace `ws` (the one the
  * preceding calls used), clear it, and return it (MP_OK if no device-side
  * error was recorded).

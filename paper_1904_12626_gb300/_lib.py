@@ -80,6 +80,7 @@ SIGNATURES = {
     "mp_backward": (ctypes.c_int, [_vp, _i32, _i64, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mp_timing_enable": (ctypes.c_int, [_i32]),
     "mp_timing_last_ms": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float)]),
+    "mp_probe_fp64_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "mp_get_device_status": (ctypes.c_int, [_vp, _vp]),
 }
 
