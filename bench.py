@@ -498,11 +498,11 @@ def run_ours(args, world, rank, local):
                      "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),
                      "frac_at_median_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
                                               if clocks.get("sm_mhz") else None),
-                     "anchors": {"tiles": tiles32, "terms": tiles32 * td.value * m,
-                                 "fp32_lane_ops": 12 * tiles32 * td.value * m,
-                                 "fp32_lane_ops_per_cell": 12 * tiles32 * td.value * m / cells,
-                                 "note": "compensated FP32 dot products (Dot2, 12 FP32 ops per "
-                                         "term) at each tile's first row, m terms per diagonal"}},
+                     "anchors": {"tiles": tiles32, "dfma": tiles32 * td.value * m,
+                                 "dfma_per_cell": tiles32 * td.value * m / cells,
+                                 "note": "exact FP64 dot products at each tile's first row: m "
+                                         "multiply-adds per diagonal, on the FP64 pipe beside "
+                                         "the FP32 work"}},
         "fp64": fp64,
         "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": {"value": e2e_value, "unit": "Gcells/s", "h2d_bytes_per_step": 4 * n,
