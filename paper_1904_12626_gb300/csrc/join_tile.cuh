@@ -690,6 +690,31 @@ __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// three-input max (one instruction in FP32; NaN operands are ignored like fmaxf's)
+__device__ __forceinline__ float vmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double vmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+
+// The largest of a row's D partial scores (three-input maxima where D = 8)
+template <int D, class T>
+__device__ __forceinline__ T row_max(const T (&tv)[D])
+{
+    if constexpr (D == 8) {
+        T m = vmax3(tv[0], tv[1], tv[2]);
+        m = vmax3(m, tv[3], tv[4]);
+        m = vmax3(m, tv[5], tv[6]);
+        return vmax(m, tv[7]);
+    } else {
+        T m = tv[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) m = vmax(m, tv[d]);
+        return m;
+    }
+}
 
 // The per-cell column test of one group of D rows, re-walked from the
 // group's starting covariances c0 (row stats at pr[u], column lane_off + s + v
@@ -726,10 +751,11 @@ static __device__ __noinline__ bool column_recheck(const typename Tr::T *c0,
 // a cell whose score reaches its row's or its column's threshold; those groups
 // are recorded (their starting covariances) and replayed exactly afterwards.
 // Per cell: two FMAs (the covariance update), one multiply (c invn_j) and one
-// max; per row, one multiply by invn_i and one compare give the exact row
-// test (the row's largest score against the row's threshold).  The column
-// test is first taken for the whole group at once: the group's largest score
-// against the smallest threshold of the 2D-1 columns it touches.  That can
+// max (three-input maxima: 4 per row of 8); per row, one multiply by invn_i and
+// one compare give the exact row test (the row's largest score against the
+// row's threshold).  The column test is first taken for the whole group at
+// once: the group's largest score against the smallest threshold of the 2D-1
+// columns it touches (tabled when the chunk is staged).  That can
 // only flag more groups than the per-cell test, so a group it flags (and the
 // row test did not) is re-walked from its starting covariances with the
 // per-cell column test before it is recorded.  The column stats walk through a
@@ -758,40 +784,35 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
     S4 cs[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) cs[d] = pc[d];
-    // smallest threshold of the columns in the ring (the group's first D columns)
-    T ringmin = cs[0].w;
-#pragma unroll
-    for (int d = 1; d < D; ++d) ringmin = vmin(ringmin, cs[d].w);
     int qn = 0;
     for (int s = s0; s < s1; s += D, pc += D + 1, pr += D) {
         T c0[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) c0[d] = c[d];
+        S4 rws[D];                              // the group's row stats
+#pragma unroll
+        for (int u = 0; u < D; ++u) rws[u] = pr[u];
         bool rowhit = false;
         T gmax = -Tr::inf();                    // the group's largest score
-        T newmin = Tr::inf();                   // columns D .. 2D-2 of the group
-        T lastw = Tr::inf();                    // column 2D-1 (the next group's ring)
 #pragma unroll
         for (int u = 0; u < D; ++u) {
-            const S4 rw = pr[u];
-            T tm = -Tr::inf();
+            const S4 &rw = rws[u];
+            T tv[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const S4 &cc = cs[(d + u) % D];
                 c[d] = Tr::fma_(rw.x, cc.y, c[d]);
                 c[d] = Tr::fma_(cc.x, rw.y, c[d]);
-                tm = vmax(tm, score_part<RAW>(c[d], cc.z));
+                tv[d] = score_part<RAW>(c[d], cc.z);
             }
-            const T M = score_finish<RAW>(tm, rw.z);
+            const T M = score_finish<RAW>(row_max<D>(tv), rw.z);
             rowhit |= (M >= rw.w);
             gmax = vmax(gmax, M);
             cs[u % D] = pc[(D + 1) + u];        // column lane_off + s + u + D
-            if (u + 1 < D) newmin = vmin(newmin, cs[u % D].w);
-            else lastw = cs[u % D].w;
         }
-        const T cmin = vmin(ringmin, newmin);
-        ringmin = vmin(newmin, lastw);
-        const bool colmaybe = gmax >= cmin;
+        // the smallest threshold of the group's 2D-1 columns, tabled at staging in
+        // the padding slot after the group's first D columns
+        const bool colmaybe = gmax >= pc[D].w;
         const bool rec = __any_sync(0xffffffffu, rowhit);
         const bool maybe = !rec && __any_sync(0xffffffffu, colmaybe);
         if (rec || maybe) {
@@ -952,6 +973,19 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                         }
                     }
                 }
+            }
+            __syncthreads();
+            // the smallest threshold of every D-aligned window of 2D-1 staged
+            // columns, into the padding slot after the window's first D columns
+            // (the fast path's group-level column test)
+            for (int q8 = threadIdx.x; q8 * D < nrr + TD; q8 += NT) {
+                T mn = Tr::inf();
+#pragma unroll
+                for (int v = 0; v < 2 * D - 1; ++v) {
+                    const int q = q8 * D + v;
+                    if (q < nrr + TD) mn = vmin(mn, (T)sCol[cpos<D>(q)].w);
+                }
+                sCol[q8 * (D + 1) + D].w = mn;
             }
             __syncthreads();
             if (r == i0 || (anchor_every > 0 && (r - i0) % anchor_every == 0)) {
