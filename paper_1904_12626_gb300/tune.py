@@ -50,6 +50,7 @@ CACHE_VERSION = 1
 TOL = {"fp32": 1e-3, "fp64": 1e-9}
 TILE_ROWS = {"fp32": (1024, 2048, 4096, 8192, 16384, 32768), "fp64": (1024, 2048, 4096, 8192)}
 DEFAULT_TILE_ROWS = {"fp32": 16384, "fp64": 4096}   # the library's defaults
+DEFAULT_TILE_ROWS_AB_FP32 = 4096                     # FP32-mixed AB-joins (shorter tiles)
 ANCHOR_DIVISORS = (2, 4, 8)
 TOP_VARIANTS = 2
 
@@ -252,8 +253,8 @@ class Tuner:
                 warnings.warn(f"{self.cache_path}: unreadable tuning cache ({e}); starting empty")
 
     # -- generic ---------------------------------------------------------
-    def tune(self, key: str, prec: str, raw: bool, run: Callable[[Candidate], Sequence[torch.Tensor]]
-             ) -> Choice:
+    def tune(self, key: str, prec: str, raw: bool, run: Callable[[Candidate], Sequence[torch.Tensor]],
+             default_tile_rows: int | None = None) -> Choice:
         """Answer `key` from the cache, else search with `run` (which runs
         the join with a candidate and returns its (mp, pi, ...) outputs)."""
         if key in self.entries:
@@ -264,6 +265,8 @@ class Tuner:
                 warnings.warn(f"tuning cache entry {key!r} is malformed; tuning again")
         from ._lib import MPError
         space = self._space_fn(prec, raw)
+        if default_tile_rows:
+            space = Space(space.variants, space.tile_rows, default_tile_rows)
         tol = TOL[prec]
         ref: list[Sequence[torch.Tensor]] = []
 
@@ -321,7 +324,8 @@ class Tuner:
         from . import api
         key = self._key("ab", prec, raw, m, [a.numel(), b.numel()])
         return self.tune(key, prec, raw, lambda c: api.abjoin(
-            a, b, m, prec, raw=raw, **c.kwargs())).kwargs()
+            a, b, m, prec, raw=raw, **c.kwargs()),
+            default_tile_rows=DEFAULT_TILE_ROWS_AB_FP32 if prec == "fp32" else None).kwargs()
 
     def batched(self, values: torch.Tensor, offsets: torch.Tensor, ms: torch.Tensor,
                 ez: float = 0.5, prec: str = "fp32", *, max_m: int | None = None) -> dict:
