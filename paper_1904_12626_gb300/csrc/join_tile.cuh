@@ -699,6 +699,13 @@ __device__ __forceinline__ float vmax3(float a, float b, float c)
 }
 __device__ __forceinline__ double vmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
 
+// Parts of a group's rows the column test takes separately (see fast_subchunk)
+template <class Tr, int D>
+__host__ __device__ constexpr int col_quarters()
+{
+    return Tr::kBias ? (D >= 4 ? 4 : D) : 1;
+}
+
 // The largest of a row's D partial scores (three-input maxima where D = 8)
 template <int D, class T>
 __device__ __forceinline__ T row_max(const T (&tv)[D])
@@ -793,7 +800,13 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
 #pragma unroll
         for (int u = 0; u < D; ++u) rws[u] = pr[u];
         bool rowhit = false;
-        T gmax = -Tr::inf();                    // the group's largest score
+        // the largest score of each quarter of the group's rows (a quarter's
+        // cells touch D/4 + D - 1 of the group's columns); FP64 compares run on
+        // the slow FP64 pipe, so the FP64 kernel takes the group whole
+        constexpr int NQ = col_quarters<Tr, D>();
+        T gq[NQ];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) gq[k] = -Tr::inf();
 #pragma unroll
         for (int u = 0; u < D; ++u) {
             const S4 &rw = rws[u];
@@ -807,12 +820,17 @@ static __device__ __noinline__ int fast_subchunk(typename Tr::T *c_io, int s0, i
             }
             const T M = score_finish<RAW>(row_max<D>(tv), rw.z);
             rowhit |= (M >= rw.w);
-            gmax = vmax(gmax, M);
+            gq[u / (D / NQ)] = vmax(gq[u / (D / NQ)], M);
             cs[u % D] = pc[(D + 1) + u];        // column lane_off + s + u + D
         }
-        // the smallest threshold of the group's 2D-1 columns, tabled at staging in
-        // the padding slot after the group's first D columns
-        const bool colmaybe = gmax >= pc[D].w;
+        // each quarter's largest score against the smallest threshold of the
+        // columns its cells touch, tabled at staging in the padding slot after
+        // the group's first D columns (x, y, z, w: quarters 0..3)
+        const S4 tq = pc[D];
+        bool colmaybe = gq[0] >= tq.x;
+        if constexpr (NQ > 1) colmaybe |= gq[1] >= tq.y;
+        if constexpr (NQ > 2) colmaybe |= gq[2] >= tq.z;
+        if constexpr (NQ > 3) colmaybe |= gq[3] >= tq.w;
         const bool rec = __any_sync(0xffffffffu, rowhit);
         const bool maybe = !rec && __any_sync(0xffffffffu, colmaybe);
         if (rec || maybe) {
@@ -975,17 +993,28 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 }
             }
             __syncthreads();
-            // the smallest threshold of every D-aligned window of 2D-1 staged
-            // columns, into the padding slot after the window's first D columns
-            // (the fast path's group-level column test)
-            for (int q8 = threadIdx.x; q8 * D < nrr + TD; q8 += NT) {
-                T mn = Tr::inf();
+            // for every D-aligned window of columns, the smallest threshold of the
+            // columns each quarter of a group's rows touches (D/4 + D - 1 columns
+            // from offset k D/4), into the padding slot after the window's first D
+            // columns (the fast path's column test)
+            {
+                constexpr int NQ = col_quarters<Tr, D>(), RQ = D / NQ;
+                for (int q8 = threadIdx.x; q8 * D < nrr + TD; q8 += NT) {
+                    T mn[4] = {Tr::inf(), Tr::inf(), Tr::inf(), Tr::inf()};
 #pragma unroll
-                for (int v = 0; v < 2 * D - 1; ++v) {
-                    const int q = q8 * D + v;
-                    if (q < nrr + TD) mn = vmin(mn, (T)sCol[cpos<D>(q)].w);
+                    for (int v = 0; v < 2 * D - 1; ++v) {
+                        const int q = q8 * D + v;
+                        const T w = q < nrr + TD ? (T)sCol[cpos<D>(q)].w : Tr::inf();
+#pragma unroll
+                        for (int k = 0; k < NQ; ++k)
+                            if (v >= k * RQ && v < k * RQ + RQ + D - 1) mn[k] = vmin(mn[k], w);
+                    }
+                    S4 &slot = sCol[q8 * (D + 1) + D];
+                    slot.x = mn[0];
+                    slot.y = mn[1];
+                    slot.z = mn[2];
+                    slot.w = mn[3];
                 }
-                sCol[q8 * (D + 1) + D].w = mn;
             }
             __syncthreads();
             if (r == i0 || (anchor_every > 0 && (r - i0) % anchor_every == 0)) {
