@@ -816,7 +816,7 @@ def run_grad(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def family_case(join: str):
+def family_case(join: str, n_series: int = 4096):
     """Inputs and call of one join family at its parity-test size (AB: a 2^21
     walk against a 2^19 walk / white-noise mix with flat stretches, m = 512;
     batched: 4096 ragged walks of 1000..65536 samples, m in {32, 64, 128};
@@ -837,7 +837,7 @@ def family_case(join: str):
                 "call": lambda xs, kw: api.abjoin(xs[0], xs[1], m, "fp32", **kw),
                 "tune": lambda tuner, xs: tuner.abjoin(xs[0], xs[1], m)}
     if join == "batched":
-        values, offsets, ms = synth.ragged_batch(4096, seed=55)
+        values, offsets, ms = synth.ragged_batch(n_series, seed=55)
         cells = 0
         for b in range(len(ms)):
             l_b = int(offsets[b + 1] - offsets[b]) - int(ms[b]) + 1
@@ -850,7 +850,7 @@ def family_case(join: str):
             mp, pi, _ = api.batched(xs[0], o_t, m_t, max_m=max_m, **kw)
             return mp, pi
         return {"inputs": [values], "cells": cells, "out_bytes": 16 * len(values),
-                "desc": "batched self-joins, 4096 random walks of 1000..65536 samples, "
+                "desc": f"batched self-joins, {n_series} random walks of 1000..65536 samples, "
                         "m in {32,64,128}",
                 "call": call,
                 "tune": lambda tuner, xs: tuner.batched(xs[0], o_t, m_t, max_m=max_m)}
@@ -949,7 +949,7 @@ def run_family(args, world, rank, local):
     lib = _lib.load()
     _lib.check(lib.mp_timing_enable(1), "mp_timing_enable")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    case = family_case(args.join)
+    case = family_case(args.join, args.series)
     kw: dict = {}                   # tile configuration (the library's defaults with --no-tune)
     tile = {"tuned": False}
     if args.tune:                   # untimed: the autotuner chooses the tile configuration
@@ -1034,6 +1034,8 @@ def main():
                     help="self-join tile variant (mp_variant_info; 0: the library default)")
     ap.add_argument("--tile-rows", type=int, default=0, help="self-join row-tile height (0: library's)")
     ap.add_argument("--anchor-every", type=int, default=0, help="self-join re-anchor interval (0: none)")
+    ap.add_argument("--series", type=int, default=4096,
+                    help="--join batched: number of series (a smaller batch for profiling)")
     ap.add_argument("--no-families", dest="families", action="store_false",
                     help="default run: skip the AB / batched / pan / gradient measurements")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
