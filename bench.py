@@ -397,9 +397,10 @@ def run_ours(args, world, rank, local):
     launches_per_step = (7 + seed_launches + 10) if anytime else (8 + seed_launches)
     td, rc = ctypes.c_int32(), ctypes.c_int32()
     prec_id = 1 if args.prec == "fp32" else 0
-    _lib.check(lib.mp_variant_info(prec_id, cfg.variant, ctypes.byref(td), ctypes.byref(rc)),
+    variant = cfg.variant if cfg.variant >= 0 else 0     # the library's choice for a self-join
+    _lib.check(lib.mp_variant_info(prec_id, variant, ctypes.byref(td), ctypes.byref(rc)),
                "mp_variant_info")
-    kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> variant {cfg.variant} "
+    kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> variant {variant} "
                    f"({td.value} diagonals x {rc.value}-row chunks)")
     step_ms, kern_ms = [], []
     kms = ctypes.c_float()
@@ -1030,8 +1031,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-s", type=float, default=12.0)
-    ap.add_argument("--variant", type=int, default=0,
-                    help="self-join tile variant (mp_variant_info; 0: the library default)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="self-join tile variant (mp_variant_info; -1: the library's choice)")
     ap.add_argument("--tile-rows", type=int, default=0, help="self-join row-tile height (0: library's)")
     ap.add_argument("--anchor-every", type=int, default=0, help="self-join re-anchor interval (0: none)")
     ap.add_argument("--series", type=int, default=4096,

@@ -53,8 +53,11 @@ typedef enum {
     MP_ENOMEM = 3,         /* workspace smaller than the size query says */
     MP_ECUDA = 4,          /* a CUDA runtime call failed */
     MP_ETIMEOUT = 5,       /* a bounded device retry loop gave up */
-    MP_EUNSUPPORTED = 6    /* no GPU of the compiled architecture, or an
+    MP_EUNSUPPORTED = 6,   /* no GPU of the compiled architecture, or an
                               unsupported tile configuration */
+    MP_EBOUNDS = 7         /* debug builds (-DMP_DEBUG) only: a device index
+                              outside its buffer was caught and the access
+                              skipped (device-detected) */
 } mp_status;
 
 typedef enum { MP_F32 = 0, MP_F64 = 1 } mp_dtype;                  /* input element type */
@@ -79,8 +82,11 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * (TR): rows per tile; 0 = the library's choice (16384 FP32-mixed, 4096
  * FP64, halved down to 1024 for joins too small to keep every CTA of the
  * persistent grid busy with that many; mp_batched keeps the default).
- * Both are rounded up to whole chunks of the variant.  variant: compiled
- * tile shape (0 = default; see mp_variant_count/mp_variant_info).  These
+ * Both are rounded up to whole chunks of the variant (the FP32-mixed AB-join
+ * and pan profile default to 4096 rows).  variant: compiled tile shape
+ * (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the library's
+ * choice: variant 1 (four warps per CTA) for FP32-mixed batched and pan joins,
+ * variant 0 otherwise.  These
  * three set the speed: the FP32-mixed path returns the same neighbours under
  * every setting, the FP64 path may break ties closer than its rounding
  * differently.  flags: MP_FLAG_*.
@@ -95,7 +101,10 @@ typedef struct {
     uint32_t flags;
 } mp_config;
 
-/* Fill `cfg` with the defaults for window m (ez 1/2, FP32-mixed, refine on). */
+#define MP_VARIANT_AUTO (-1)
+
+/* Fill `cfg` with the defaults for window m (ez 1/2, FP32-mixed, refine on,
+ * tile shape and height left to the library). */
 void mp_config_default(mp_config *cfg, int32_t m);
 
 /* Host helpers, no GPU needed.  l = n - m + 1 (0 if m > n or m < 1), per the

@@ -13,7 +13,7 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libmpgb.so")
 
-MP_OK, MP_EINVAL, MP_EINVAL_DATA, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT, MP_EUNSUPPORTED = range(7)
+MP_OK, MP_EINVAL, MP_EINVAL_DATA, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT, MP_EUNSUPPORTED, MP_EBOUNDS = range(8)
 MP_F32, MP_F64 = 0, 1
 MP_PREC_FP64, MP_PREC_FP32_MIXED = 0, 1
 MP_FLAG_EXCL_INCLUSIVE = 0x1
@@ -118,7 +118,7 @@ def check(code: int, where: str) -> None:
 
 
 def make_config(m: int, ez: float = 0.5, prec: str = "fp32", anchor_every: int = 0,
-                tile_rows: int = 0, variant: int = 0, flags: int = 0) -> MPConfig:
+                tile_rows: int = 0, variant: int = -1, flags: int = 0) -> MPConfig:
     cfg = MPConfig()
     load().mp_config_default(ctypes.byref(cfg), int(m))
     cfg.ez = float(ez)

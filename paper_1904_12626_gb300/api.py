@@ -75,7 +75,7 @@ def stats(x: torch.Tensor, m: int, stream=None):
 
 def selfjoin(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *, refine: bool = True,
              inclusive: bool = False, raw: bool = False, tile_rows: int = 0, anchor_every: int = 0,
-             variant: int = 0, ws: torch.Tensor | None = None, stream=None,
+             variant: int = -1, ws: torch.Tensor | None = None, stream=None,
              check_status: bool = False):
     """Self-join matrix profile of one series.  Returns (mp float64, pi int64).
     raw=True: the non-normalised distance ||x_i - x_j|| (SiMPle)."""
@@ -102,7 +102,7 @@ def selfjoin(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *, re
 
 def selfjoin_lr(x: torch.Tensor, m: int, ez: float = 0.5, prec: str = "fp32", *,
                 refine: bool = True, inclusive: bool = False, raw: bool = False,
-                tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
+                tile_rows: int = 0, anchor_every: int = 0, variant: int = -1,
                 ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
     """Left and right self-join profiles.  Returns (mp_left, pi_left, mp_right, pi_right):
     the nearest neighbour of each window among the windows before / after it."""
@@ -133,7 +133,7 @@ class Anytime:
     cumulative fraction at a time.  `run(f)` returns the best-so-far (mp, pi)."""
 
     def __init__(self, x: torch.Tensor, m: int, seed: int = 0, ez: float = 0.5,
-                 prec: str = "fp32", *, variant: int = 0, tile_rows: int = 0, stream=None,
+                 prec: str = "fp32", *, variant: int = -1, tile_rows: int = 0, stream=None,
                  ws: torch.Tensor | None = None):
         self.x = _prep(x, "x")
         self.lib = _lib.load()
@@ -190,7 +190,7 @@ def fluss(pi: torch.Tensor, m: int, num_segments: int = 2, *, edge: int | None =
 
 def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refine: bool = True,
            both: bool = True, raw: bool = False, tile_rows: int = 0, anchor_every: int = 0,
-           variant: int = 0, ws: torch.Tensor | None = None, stream=None,
+           variant: int = -1, ws: torch.Tensor | None = None, stream=None,
            check_status: bool = False):
     """AB-join.  Returns (mp_a, pi_a, mp_b, pi_b); the B side is None unless `both`."""
     a = _prep(a, "a")
@@ -222,7 +222,7 @@ def abjoin(a: torch.Tensor, b: torch.Tensor, m: int, prec: str = "fp32", *, refi
 
 def batched(values: torch.Tensor, offsets: torch.Tensor, ms: torch.Tensor, ez: float = 0.5,
             prec: str = "fp32", *, refine: bool = True, tile_rows: int = 0, anchor_every: int = 0,
-            variant: int = 0, out_offsets: torch.Tensor | None = None, max_m: int | None = None,
+            variant: int = -1, out_offsets: torch.Tensor | None = None, max_m: int | None = None,
             ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
     """Self-joins of B ragged series in one persistent launch.
 
@@ -260,7 +260,7 @@ def batched(values: torch.Tensor, offsets: torch.Tensor, ms: torch.Tensor, ez: f
 
 
 def pan(x: torch.Tensor, ms, ez: float = 0.5, prec: str = "fp32", *, refine: bool = True,
-        normalize: bool = False, tile_rows: int = 0, anchor_every: int = 0, variant: int = 0,
+        normalize: bool = False, tile_rows: int = 0, anchor_every: int = 0, variant: int = -1,
         ws: torch.Tensor | None = None, stream=None, check_status: bool = False):
     """Pan matrix profile over window sizes `ms` (host ints).  Returns
     (pan [nm x (n - min(ms) + 1)] float64, pi int64), +inf / -1 padded."""

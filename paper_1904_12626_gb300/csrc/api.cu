@@ -20,6 +20,14 @@ constexpr int kDefaultTileRowsF64 = 4096;
 // raised (2^21 x 2^19 walk / white-noise mix, m = 512, variant 0: 450 ms at
 // 4096 rows, 550 ms at 8192, 654 ms at 16384).
 constexpr int kDefaultTileRowsAbF32 = 4096;
+// The tile shape MP_VARIANT_AUTO stands for in the batched and pan joins: four
+// warps per CTA (1024 diagonals per band; on 4096 ragged walks 1941 ms against
+// 2024 ms with the two-warp default, on 64 window sizes of a 2^16 walk 111
+// against 117 ms at 4096-row tiles).  The self-, left/right and AB-joins keep 0.
+constexpr int kAutoVariantFamilies = 1;
+// FP32-mixed pan profiles: 4096-row tiles by default, for the AB-join's reason
+// (variant 1: 111 ms against 114 ms at 16384 rows)
+constexpr int kDefaultTileRowsPanF32 = 4096;
 constexpr long long kMaxN = 2147483647ll;
 
 struct DeviceInfo {
@@ -84,14 +92,18 @@ struct TileCfg {
     bool raw;                // MP_FLAG_RAW: non-normalised distance (variant 0 only)
 };
 
-mp_status resolve(const mp_config *cfg, TileCfg *t)
+// auto_variant: the tile shape MP_VARIANT_AUTO stands for in this family
+// (FP32-mixed only; the FP64 path and the non-normalised distance take 0)
+mp_status resolve(const mp_config *cfg, TileCfg *t, int auto_variant = 0)
 {
     if (!cfg) return MP_EINVAL;
     if (cfg->prec != MP_PREC_FP64 && cfg->prec != MP_PREC_FP32_MIXED) return MP_EINVAL;
     if (!(cfg->ez >= 0.0) || !std::isfinite(cfg->ez)) return MP_EINVAL;
     if (cfg->anchor_every < 0 || cfg->tile_rows < 0) return MP_EINVAL;
     t->fp64 = cfg->prec == MP_PREC_FP64;
-    t->variant = cfg->variant;
+    const bool raw_flag = (cfg->flags & MP_FLAG_RAW) != 0;
+    t->variant = cfg->variant >= 0 ? cfg->variant
+                                   : ((t->fp64 || raw_flag) ? 0 : auto_variant);
     int threads = 0, smem = 0;
     const bool ok = t->fp64 ? f64_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem)
                             : f32_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem);
@@ -342,7 +354,7 @@ void mp_config_default(mp_config *cfg, int32_t m)
     cfg->prec = MP_PREC_FP32_MIXED;
     cfg->anchor_every = 0;
     cfg->tile_rows = 0;
-    cfg->variant = 0;
+    cfg->variant = MP_VARIANT_AUTO;
     cfg->flags = 0;
 }
 
@@ -382,6 +394,7 @@ const char *mp_status_string(mp_status st)
     case MP_ECUDA: return "CUDA runtime error";
     case MP_ETIMEOUT: return "device retry limit reached";
     case MP_EUNSUPPORTED: return "unsupported device or configuration";
+    case MP_EBOUNDS: return "device index out of bounds (debug build)";
     }
     return "unknown status";
 }
@@ -604,7 +617,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
 size_t mp_pan_workspace_bytes(int64_t n, const int32_t *ms, int32_t nm, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t) != MP_OK || !ms || nm < 1 || nm > kMaxPan || n < 1) return 0;
+    if (resolve(cfg, &t, kAutoVariantFamilies) != MP_OK || !ms || nm < 1 || nm > kMaxPan || n < 1) return 0;
     for (int k = 0; k < nm; ++k)
         if (ms[k] < 4 || ms[k] > n) return 0;
     return carve(nullptr, pan_req(n, ms, nm, t)).bytes;
@@ -622,7 +635,7 @@ mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int
         if (ms[k] < 4 || (int64_t)ms[k] > n) return MP_EINVAL;
         if (ms[k] < mmin) mmin = ms[k];
     }
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, kAutoVariantFamilies);
     if (s != MP_OK) return s;
     const LayoutReq r = pan_req(n, ms, nm, t);
     const Layout L = carve(ws, r);
@@ -643,6 +656,10 @@ mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int
     MP_CU(launch_family_descs(F, st));
     double cells = 0.0;
     for (int k = 0; k < nm; ++k) cells += self_cells(n, ms[k], cfg->ez);
+    if (cfg->tile_rows <= 0 && !t.fp64) {
+        t.tile_rows = (int)(ceil_div(kDefaultTileRowsPanF32, t.chunk_rows) * t.chunk_rows);
+        if (t.anchor_every >= t.tile_rows) t.anchor_every = 0;
+    }
     fit_tile_rows(cfg, &t, cells, d);
     return run_join(L, r, t, n - mmin + 1, d, st);
 }
@@ -652,7 +669,7 @@ size_t mp_batched_workspace_bytes(int64_t total_values, int32_t B, int32_t max_m
 {
     TileCfg t;
     (void)max_m;
-    if (resolve(cfg, &t) != MP_OK || B < 1 || total_values < 0) return 0;
+    if (resolve(cfg, &t, kAutoVariantFamilies) != MP_OK || B < 1 || total_values < 0) return 0;
     return carve(nullptr, batched_req(total_values, B, t)).bytes;
 }
 
@@ -666,7 +683,7 @@ mp_status mp_batched(const void *values, int32_t dtype, int64_t total_values,
         !aligned256(ws))
         return MP_EINVAL;
     if (B < 1 || B > 65535 || total_values < 1 || total_values > kMaxN || max_m < 4) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, kAutoVariantFamilies);
     if (s != MP_OK) return s;
     const LayoutReq r = batched_req(total_values, B, t);
     const Layout L = carve(ws, r);
