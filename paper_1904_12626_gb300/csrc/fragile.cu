@@ -117,6 +117,7 @@ fragile_pass_kernel(const StatSet *__restrict__ sets, const double *__restrict__
         const long long f = (long long)(ent & ((1ull << 40) - 1));
         const StatSet SX = sets[xs];
         const StatSet SY = sets[SX.partner];
+        if (!index_ok(hdr, f, SX.l)) continue;                    // block-uniform: one entry per block
         const int m = SX.m;
         const double *xf = SX.x + f;
         // level L: whichever end value the window repeats more often

@@ -183,6 +183,23 @@ __device__ __forceinline__ void set_status(Hdr *h, unsigned st)
     atomicCAS(&h->status, 0u, st);
 }
 
+// Debug builds (-DMP_DEBUG): is index i inside [0, lim)?  If not, record
+// MP_EBOUNDS and let the caller skip the access.  Release builds: always true,
+// so the check compiles to nothing.
+__device__ __forceinline__ bool index_ok(Hdr *h, long long i, long long lim)
+{
+#ifdef MP_DEBUG
+    if (i >= 0 && i < lim) return true;
+    set_status(h, MP_EBOUNDS);
+    return false;
+#else
+    (void)h;
+    (void)i;
+    (void)lim;
+    return true;
+#endif
+}
+
 // order-preserving map of a float's bits to an unsigned integer
 __host__ __device__ __forceinline__ unsigned ord32(unsigned u)
 {

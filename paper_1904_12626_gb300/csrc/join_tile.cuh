@@ -314,7 +314,7 @@ __device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
         Packed best = Tr::pzero();
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            if (colc[d]) {
+            if (colc[d] && index_ok(hdr, i + kl + d, P.lC)) {
                 const long long j = i + kl + d;
                 const int q = cpos<D>(lane_off + s + u + d);
                 Tr::merge(cKey, j, Tr::pack(rho[d], i), hdr);
@@ -333,7 +333,7 @@ __device__ __noinline__ void replay_group(const Prob &P, typename Tr::S4 *sRow,
             const Packed y = Tr::pshfl(best, o);
             if (Tr::pgt(y, best)) best = y;
         }
-        if (lane == 0 && Tr::pgt(best, Tr::pzero())) {
+        if (lane == 0 && Tr::pgt(best, Tr::pzero()) && index_ok(hdr, i, P.lR)) {
             Tr::merge(rKey, i, best, hdr);
             const T v = Tr::pval(best);
             if (v > sRow[s + u].w) {
@@ -391,7 +391,8 @@ static __device__ __noinline__ void warp_merge(const Prob &P, bool pending, Cand
             mask &= mask - 1;
             const long long a = __shfl_sync(0xffffffffu, row_side ? own : c.idx, src);
             const long long b = __shfl_sync(0xffffffffu, row_side ? c.idx : own, src);
-            const float e = (float)exact_correlation(P, a, b, lane);
+            const bool ok = index_ok(hdr, a, P.lR) & index_ok(hdr, b, P.lC);   // warp-uniform
+            const float e = ok ? (float)exact_correlation(P, a, b, lane) : 0.0f;
             if (lane == src) c.V = c.L = e;
         }
         mask = __ballot_sync(0xffffffffu, need_k);
@@ -400,7 +401,8 @@ static __device__ __noinline__ void warp_merge(const Prob &P, bool pending, Cand
             mask &= mask - 1;
             const long long a = __shfl_sync(0xffffffffu, row_side ? own : kpair, src);
             const long long b = __shfl_sync(0xffffffffu, row_side ? kpair : own, src);
-            const float e = (float)exact_correlation(P, a, b, lane);
+            const bool ok = index_ok(hdr, a, P.lR) & index_ok(hdr, b, P.lC);   // warp-uniform
+            const float e = ok ? (float)exact_correlation(P, a, b, lane) : 0.0f;
             if (lane == src) {
                 kx = e;
                 kx_idx = kpair;
@@ -580,7 +582,8 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
                     const long long j = __shfl_sync(0xffffffffu, i + kl + d, src);
                     const bool ns = __shfl_sync(0xffffffffu, need_s, src);
                     const bool nr = __shfl_sync(0xffffffffu, need_r, src);
-                    const float e = (float)exact_correlation(P, i, j, lane);
+                    const bool ok = index_ok(hdr, i, P.lR) & index_ok(hdr, j, P.lC);
+                    const float e = ok ? (float)exact_correlation(P, i, j, lane) : 0.0f;
                     if (ns && lane == src) {
                         const unsigned long long p = TraitsF32::pack(e, i);
                         if (p > ex_l[o]) ex_l[o] = p;
@@ -641,7 +644,9 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
             j = r + s + k0 + src_off + o;
             q = src_off + s + o;
         }
-        warp_merge(P, has, c, cKey + j, false, j, cS + j, sCol + cpos<D>(q), lane, hdr);
+        const bool in = has && index_ok(hdr, j, P.lC);
+        warp_merge(P, in, c, cKey + (in ? j : 0), false, j, cS + (in ? j : 0), sCol + cpos<D>(q), lane,
+                   hdr);
         __syncwarp();
     }
 
@@ -660,8 +665,8 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
         }
     }
     const long long ir = r + s + (lane < D ? lane : 0);
-    warp_merge(P, rc.idx >= 0, rc, rKey + ir, true, ir, rS + ir, sRow + s + (lane < D ? lane : 0),
-               lane, hdr);
+    const bool rin = rc.idx >= 0 && index_ok(hdr, ir, P.lR);
+    warp_merge(P, rin, rc, rKey + ir, true, ir, rS + ir, sRow + s + (lane < D ? lane : 0), lane, hdr);
     __syncwarp();
 }
 
@@ -948,7 +953,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     S4 v[U];
 #pragma unroll
                     for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < nrr) v[k] = Tr::ld(rS + r + t0 + k * NT);
+                        if (t0 + k * NT < nrr && index_ok(hdr, r + t0 + k * NT, lR + kPad))
+                            v[k] = Tr::ld(rS + r + t0 + k * NT);
 #pragma unroll
                     for (int k = 0; k < U; ++k)
                         if (t0 + k * NT < nrr) {
@@ -962,7 +968,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     S4 v[U];
 #pragma unroll
                     for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < ncols) v[k] = Tr::ld(cS + cb + t0 + k * NT);
+                        if (t0 + k * NT < ncols && index_ok(hdr, cb + t0 + k * NT, lC + kPad))
+                            v[k] = Tr::ld(cS + cb + t0 + k * NT);
 #pragma unroll
                     for (int k = 0; k < U; ++k)
                         if (t0 + k * NT < ncols) {
@@ -1021,7 +1028,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 // covariance at row a = r - 1 so that row r applies the update; at
                 // r = 0 the update of row 0 adds 0 (df_0 = dg_0 = 0)
                 const long long a = r > 0 ? r - 1 : 0;
-                anchor_covariances<Tr, D>(P, a, a + kl, c);
+                if (index_ok(hdr, a, lR)) anchor_covariances<Tr, D>(P, a, a + kl, c);
                 e_c = 0.0f;
                 e_applied = 0.0f;
                 e_steps = 0;
