@@ -3,8 +3,8 @@
 
 Workload: self-join of a 2^20-sample float32 random walk with three planted
 motif pairs and a planted discord, window m = 256, exclusion zone
-ceil(m/2) = 128, in the FP32-mixed precision (FP64 statistics, anchors and
-distances; FP32 diagonal recurrence).  One step = one whole mp_selfjoin
+ceil(m/2) = 128, in the FP32-mixed precision (FP64 statistics and distances;
+FP32 diagonal recurrence and anchors on FP64-centred values).  One step = one whole mp_selfjoin
 (input conversion, statistics, tile planning, the persistent diagonal-tile
 kernel, finalize with the exact FP64 refine) on input already resident in
 HBM.  The all-FP64 kernel is timed on the same input for comparison.
@@ -513,7 +513,7 @@ def run_ours(args, world, rank, local):
         "value": value, "unit": "Gcells/s", "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 stats, centring and refine)",
         "data": "synthetic", "config": config_block(args, E, cells),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": ("T FP32 lane-instructions/s (6 per cell: 2 FFMA, "
@@ -525,11 +525,13 @@ def run_ours(args, world, rank, local):
                      "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),
                      "frac_at_median_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
                                               if clocks.get("sm_mhz") else None),
-                     "anchors": {"tiles": tiles32, "dfma": tiles32 * td.value * m,
-                                 "dfma_per_cell": tiles32 * td.value * m / cells,
-                                 "note": "exact FP64 dot products at each tile's first row: m "
-                                         "multiply-adds per diagonal, on the FP64 pipe beside "
-                                         "the FP32 work"}},
+                     "anchors": {"tiles": tiles32, "ffma": tiles32 * td.value * m,
+                                 "ffma_per_cell": tiles32 * td.value * m / cells,
+                                 "note": "dot products at each tile's first row: m FP32 "
+                                         "multiply-adds per diagonal on values centred in "
+                                         "FP64 (about 1.5 more FP32 instructions per term for "
+                                         "the centring shift and the bound); their rounding "
+                                         "widens the error bias"}},
         "fp64": fp64,
         "fp32_vs_fp64": (value / fp64["value"]) if fp64 else None,
         "e2e": {"value": e2e_value, "unit": "Gcells/s", "h2d_bytes_per_step": 4 * n,
@@ -796,7 +798,7 @@ def run_grad(args, world, rank, local):
         "value": replica_value(world, cells, args.steps, total_ms), "unit": "Gcells/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 forward (FP64 stats/anchors/refine), f64 backward",
+        "vs_baseline": None, "dtype": "f32 forward (FP64 stats, centring and refine), f64 backward",
         "data": "synthetic",
         "config": {"workload": f"random walk n={n} float32, m={m}, loss = sum(MP) + mean(top-16 MP)",
                    "cells": cells, "l2": "flushed between timed steps (512 MiB write)"},
@@ -995,7 +997,7 @@ def run_family(args, world, rank, local):
         "value": replica_value(world, cells, args.steps, total_ms), "unit": "Gcells/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (FP64 stats/anchors/refine)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 (FP64 stats, centring and refine)", "data": "synthetic",
         "config": {"workload": case["desc"], "cells": cells, "tile": tile,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,

@@ -40,8 +40,10 @@
 // q - h_i - h_j (2 subtractions instead of the 2 multiplies), see internal.cuh.
 //
 // Anchors.  The first covariance of each diagonal in a tile, and every
-// `anchor_every` rows after it, is an exact FP64 dot product of the two
-// windows; in the FP32-mixed instantiation only the recurrence runs in FP32.
+// `anchor_every` rows after it, is a dot product of the two windows: exact
+// FP64 in the FP64 instantiation; in the FP32-mixed one an FP32 dot product of
+// values centred in FP64 (anchor_covariances_f32), whose rounding enters the
+// error bias like m more steps of the recurrence.
 #pragma once
 
 #include <cmath>
@@ -271,6 +273,98 @@ __device__ __forceinline__ void track_max(float *mx, float *hmax, const S4 &v)
 // smem index of staged column q (one padding slot every D entries)
 template <int D>
 __device__ __forceinline__ int cpos(int q) { return q + q / D; }
+
+// Terms of an FP32-mixed anchor staged in shared memory per pass.
+constexpr int kAnchorTerms = 512;
+
+// FP32-mixed anchors: covariances c(a, j0 + d), j0 = a + k0 + lane_off, for
+// the D diagonals of every thread of the CTA (all threads call this together;
+// it uses the chunk staging area and ends with a barrier).  The same
+// centred-row identity as the FP64 anchors: sum_t (x_{a+t} - mu_a) y_{j+t}
+// equals sum_t (x_{a+t} - mu_a)(y_{j+t} - g) for any constant g.  The row
+// values a_t = x_{a+t} - mu_a are formed in FP64 and rounded to FP32; the
+// column values are formed in FP64 against the CTA's reference g0 (the mean
+// of its middle column window) and staged as FP32 hi + lo pairs, and each
+// thread shifts them to its own reference g (the mean of its middle window)
+// in FP32 (b_j = (hi_j - g_hi) + (lo_j - g_lo)), so that its products are
+// those of nearly centred windows and the running sums stay near the size of
+// the result.  The dot products then run as FP32 FMA chains.  Their rounding
+// is bounded like the recurrence's (each step rounds a partial sum at most
+// B = ||a|| ||b|| in size), so the caller adds B sqrt(m + 4) to the error
+// bias; returned: B, the largest over the warp (the replay shares one bias per
+// warp).  The FP32 pipe runs these 64 times faster than FP64 multiply-adds on
+// this GPU, which matters where m is large against the tile height.
+template <int D, int NT>
+static __device__ __noinline__ float anchor_covariances_f32(const Prob &P, long long a, long long k0,
+                                                            float *c_out)
+{
+    constexpr int TD = NT * D;
+    constexpr int MT = kAnchorTerms;
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    float *sA = reinterpret_cast<float *>(smem_raw);
+    float *sHi = sA + MT;
+    float *sLo = sHi + cpos<D>(TD + MT);
+    const int tid = threadIdx.x;
+    const int lane_off = tid * D;
+    const int m = P.m;
+    const long long last = P.nC - 1;
+    const long long lastw = P.lC - 1;
+    const long long cb = a + k0;                 // column of diagonal k0 at row a
+    const double mu = P.rMu[a];
+    const long long wr = cb + TD / 2;
+    const double g0 = P.cMu[wr < lastw ? wr : lastw];
+    const long long wt = cb + lane_off + D / 2;
+    const double dg = (wt <= lastw ? P.cMu[wt] : g0) - g0;
+    const float g_hi = (float)dg, g_lo = (float)(dg - (double)g_hi);
+    float acc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) acc[d] = 0.0f;
+    float sa = 0.0f, sb = 0.0f;
+    for (int tb = 0; tb < m; tb += MT) {
+        const int mt = min(MT, m - tb);
+        const int mtp = (mt + D - 1) / D * D;    // padded with a_t = 0
+        for (int q = tid; q < mtp; q += NT)
+            sA[q] = q < mt ? (float)(P.rX[a + tb + q] - mu) : 0.0f;
+        const int nb = TD + mtp - 1;             // column values lane_off + t + d
+        for (int q = tid; q < nb; q += NT) {
+            long long j = cb + tb + q;
+            j = j < last ? j : last;
+            const double v = P.cX[j] - g0;
+            const float h = (float)v;
+            sHi[cpos<D>(q)] = h;
+            sLo[cpos<D>(q)] = (float)(v - (double)h);
+        }
+        __syncthreads();
+        // ring of column values: diagonal d at step t reads slot (t + d) mod D
+        float b[D];
+#pragma unroll
+        for (int v = 0; v < D - 1; ++v) {
+            const int q = cpos<D>(lane_off + v);
+            b[v] = (sHi[q] - g_hi) + (sLo[q] - g_lo);
+            sb = fmaf(b[v], b[v], sb);
+        }
+        for (int t = 0; t < mtp; t += D) {
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int q = cpos<D>(lane_off + t + u + D - 1);
+                const float bn = (sHi[q] - g_hi) + (sLo[q] - g_lo);
+                b[(u + D - 1) % D] = bn;
+                sb = fmaf(bn, bn, sb);
+                const float at = sA[t + u];
+                sa = fmaf(at, at, sa);
+#pragma unroll
+                for (int d = 0; d < D; ++d) acc[d] = fmaf(at, b[(u + d) % D], acc[d]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) c_out[d] = (cb + lane_off + d < P.lC) ? acc[d] : 0.0f;
+    float bnd = sqrtf(sa) * sqrtf(sb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bnd = fmaxf(bnd, __shfl_xor_sync(0xffffffffu, bnd, o));
+    return bnd;
+}
 
 
 template <class T, int D>
@@ -932,9 +1026,12 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
         // Rounding errors of N steps behave like a random walk: their standard
         // deviation is about 0.41 eps sqrt(N) |c|, with |c| <= s_i s_j.  E uses
         // the chunks' RMS norms and update terms (largest RMS since the anchor)
-        // and about five standard deviations:
-        //   E = kBiasSigma eps C sqrt(N + 16),  C = s_R s_C + 2 (df_R dg_C + df_C dg_R).
+        // and about five standard deviations, combined in quadrature with the
+        // FP32 anchor's rounding (m FMA steps on partial sums of at most B):
+        //   E = kBiasSigma eps hypot(C sqrt(N + 16), B sqrt(m + 4)),
+        //   C = s_R s_C + 2 (df_R dg_C + df_C dg_R).
         float e_c = 0.0f, e_applied = 0.0f;
+        float e_anchor = 0.0f;                   // FP32 anchors: B sqrt(m + 4)
         int e_steps = 0;
         int chunk = 0;
         for (long long r = i0; r < i1; r += RC, ++chunk) {
@@ -942,6 +1039,26 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
             const int nrr = (nrows + D - 1) / D * D;
             const int par = (chunk & 1) * 12;
             __syncthreads();
+            const bool anchor_here = r == i0 || (anchor_every > 0 && (r - i0) % anchor_every == 0);
+            if constexpr (Tr::kBias) {
+                // covariance at row a = r - 1 so that row r applies the update; at
+                // r = 0 the update of row 0 adds 0 (df_0 = dg_0 = 0).  The FP32
+                // anchors use the staging area, so they run before the staging.
+                if (anchor_here) {
+                    const long long a = r > 0 ? r - 1 : 0;
+                    float bnd = 0.0f;
+                    if (index_ok(hdr, a, lR)) {
+                        static_assert(kAnchorTerms + 2 * (TD + kAnchorTerms + kAnchorTerms / D + TD / D) <=
+                                          Sh::SMEM_STATS / 4,
+                                      "anchor staging larger than the chunk staging area");
+                        bnd = anchor_covariances_f32<D, NT>(P, a, k0, c);
+                    }
+                    e_c = 0.0f;
+                    e_applied = 0.0f;
+                    e_steps = 0;
+                    e_anchor = bnd * sqrtf((float)(P.m + 4));
+                }
+            }
             // stage {df, dg, invn, thr} of the chunk's rows and columns: plain
             // copies (L2 reads, so thresholds raised by other CTAs are seen),
             // loads batched ahead of the stores
@@ -1024,9 +1141,8 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 }
             }
             __syncthreads();
-            if (r == i0 || (anchor_every > 0 && (r - i0) % anchor_every == 0)) {
-                // covariance at row a = r - 1 so that row r applies the update; at
-                // r = 0 the update of row 0 adds 0 (df_0 = dg_0 = 0)
+            if (!Tr::kBias && anchor_here) {
+                // as above, exact FP64
                 const long long a = r > 0 ? r - 1 : 0;
                 if (index_ok(hdr, a, lR)) anchor_covariances<Tr, D>(P, a, a + kl, c);
                 e_c = 0.0f;
@@ -1045,8 +1161,12 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 // RAW adds a bound on this chunk's FP32 rounding of h_i, h_j and of
                 // the score's two subtractions: about 3 eps (h_i + h_j) / 2 at most,
                 // covered by 2 kBiasSigma eps (largest h of the rows + of the columns)
-                const float e = kBiasSigma * (float)Tr::kEps *
-                                (e_c * sqrtf((float)(e_steps + 16)) + 2.0f * hsum);
+                // the anchor's rounding adds in quadrature (independent of the
+                // recurrence's); hypot form, so no square overflows
+                const float er = e_c * sqrtf((float)(e_steps + 16));
+                const float eh = fmaxf(er, e_anchor), el = fminf(er, e_anchor);
+                const float q = eh > 0.0f ? el / eh : 0.0f;
+                const float e = kBiasSigma * (float)Tr::kEps * (eh * sqrtf(1.0f + q * q) + 2.0f * hsum);
                 const T inc = (T)(e - e_applied);
                 e_applied = e;
 #pragma unroll
