@@ -83,10 +83,11 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * FP64, halved down to 1024 for joins too small to keep every CTA of the
  * persistent grid busy with that many; mp_batched keeps the default).
  * Both are rounded up to whole chunks of the variant (the FP32-mixed AB-join
- * and pan profile default to 4096 rows).  variant: compiled tile shape
- * (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the library's
- * choice: variant 1 (four warps per CTA) for FP32-mixed batched and pan joins,
- * variant 0 otherwise.  These
+ * defaults to 2048 rows, the pan profile to 4096).  variant: compiled tile
+ * shape (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the
+ * library's choice: variant 7 (four warps per CTA, 5 CTAs per SM) for
+ * FP32-mixed AB-joins, variant 1 (four warps per CTA) for FP32-mixed batched
+ * and pan joins, variant 0 otherwise.  These
  * three set the speed: the FP32-mixed path returns the same neighbours under
  * every setting, the FP64 path may break ties closer than its rounding
  * differently.  flags: MP_FLAG_*.

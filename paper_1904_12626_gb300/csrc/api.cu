@@ -17,9 +17,13 @@ constexpr int kDefaultTileRowsF64 = 4096;
 // FP32-mixed AB-joins: shorter row tiles by default.  Both series' keys improve
 // as bands complete, and short tiles let the bands of a problem finish nearly in
 // the order they start, so each band starts from thresholds its predecessors
-// raised (2^21 x 2^19 walk / white-noise mix, m = 512, variant 0: 450 ms at
-// 4096 rows, 550 ms at 8192, 654 ms at 16384).
-constexpr int kDefaultTileRowsAbF32 = 4096;
+// raised (2^21 x 2^19 walk / white-noise mix, m = 512, tile kernel ms at 1024 /
+// 2048 / 4096 / 8192 rows: variant 0 358 / 347 / 355 / 476, variant 7 333 / 323
+// / 331 / 445).
+constexpr int kDefaultTileRowsAbF32 = 2048;
+// The tile shape MP_VARIANT_AUTO stands for in FP32-mixed AB-joins: four warps
+// per CTA at 5 CTAs per SM (variant 7, figures above).
+constexpr int kAutoVariantAb = 7;
 // The tile shape MP_VARIANT_AUTO stands for in the batched and pan joins: four
 // warps per CTA (1024 diagonals per band; on 4096 ragged walks 1941 ms against
 // 2024 ms with the two-warp default, on 64 window sizes of a 2^16 walk 111
@@ -573,7 +577,7 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
 size_t mp_abjoin_workspace_bytes(int64_t na, int64_t nb, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t) != MP_OK || na < 1 || nb < 1) return 0;
+    if (resolve(cfg, &t, kAutoVariantAb) != MP_OK || na < 1 || nb < 1) return 0;
     return carve(nullptr, ab_req(na, nb, cfg->m, t)).bytes;
 }
 
@@ -584,7 +588,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
     TileCfg t;
     if (!a || !b || !mp_a || !pi_a || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
     if ((mp_b == nullptr) != (pi_b == nullptr)) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, kAutoVariantAb);
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > na || (int64_t)m > nb || na > kMaxN || nb > kMaxN) return MP_EINVAL;

@@ -262,12 +262,30 @@ __device__ __forceinline__ void track_max(float *mx, float *hmax, const S4 &v)
 {
     const float z = (float)v.z;
     if (RAW ? (z == z) : (z > 0.f)) {
-        mx[0] += RAW ? 2.0f * z : 1.0f / (z * z);
+        mx[0] += RAW ? 2.0f * z : __fdividef(1.0f, z * z);   // an RMS estimate: approximate is fine
         mx[1] += (float)v.x * (float)v.x;
         mx[2] += (float)v.y * (float)v.y;
         mx[3] += 1.0f;
         if (RAW) *hmax = fmaxf(*hmax, z);
     }
+}
+
+// Asynchronous 16-byte global -> shared copies (L2 reads: thresholds other CTAs
+// raised are seen) of one packed statistics entry; stage_wait() completes this
+// thread's copies (other threads' need a barrier after it).
+template <class S4>
+__device__ __forceinline__ void stage_async(S4 *dst, const S4 *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+#pragma unroll
+    for (int h = 0; h < (int)(sizeof(S4) / 16); ++h)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * h), "l"(g + 16 * h)
+                     : "memory");
+}
+__device__ __forceinline__ void stage_wait()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // smem index of staged column q (one padding slot every D entries)
@@ -1059,40 +1077,22 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                     e_anchor = bnd * sqrtf((float)(P.m + 4));
                 }
             }
-            // stage {df, dg, invn, thr} of the chunk's rows and columns: plain
-            // copies (L2 reads, so thresholds raised by other CTAs are seen),
-            // loads batched ahead of the stores
+            // stage {df, dg, invn, thr} of the chunk's rows and columns: copies
+            // from L2 (so thresholds raised by other CTAs are seen), all of a
+            // thread's issued at once as asynchronous copies (one round trip)
             {
-                constexpr int U = 4;
                 float mx[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float hm[2] = {0.f, 0.f};
-                for (int t0 = threadIdx.x; t0 < nrr; t0 += NT * U) {
-                    S4 v[U];
-#pragma unroll
-                    for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < nrr && index_ok(hdr, r + t0 + k * NT, lR + kPad))
-                            v[k] = Tr::ld(rS + r + t0 + k * NT);
-#pragma unroll
-                    for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < nrr) {
-                            sRow[t0 + k * NT] = v[k];
-                            if (Tr::kBias) track_max<RAW>(mx, hm, v[k]);
-                        }
-                }
                 const long long cb = r + k0;
                 const int ncols = nrr + TD;
-                for (int t0 = threadIdx.x; t0 < ncols; t0 += NT * U) {
-                    S4 v[U];
-#pragma unroll
-                    for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < ncols && index_ok(hdr, cb + t0 + k * NT, lC + kPad))
-                            v[k] = Tr::ld(cS + cb + t0 + k * NT);
-#pragma unroll
-                    for (int k = 0; k < U; ++k)
-                        if (t0 + k * NT < ncols) {
-                            sCol[cpos<D>(t0 + k * NT)] = v[k];
-                            if (Tr::kBias) track_max<RAW>(mx + 4, hm + 1, v[k]);
-                        }
+                for (int t = threadIdx.x; t < nrr; t += NT)
+                    if (index_ok(hdr, r + t, lR + kPad)) stage_async(sRow + t, rS + r + t);
+                for (int t = threadIdx.x; t < ncols; t += NT)
+                    if (index_ok(hdr, cb + t, lC + kPad)) stage_async(sCol + cpos<D>(t), cS + cb + t);
+                stage_wait();
+                if (Tr::kBias) {                       // this thread's own entries
+                    for (int t = threadIdx.x; t < nrr; t += NT) track_max<RAW>(mx, hm, sRow[t]);
+                    for (int t = threadIdx.x; t < ncols; t += NT) track_max<RAW>(mx + 4, hm + 1, sCol[cpos<D>(t)]);
                 }
                 if (Tr::kBias) {                       // warp sums, then one add per warp
 #pragma unroll

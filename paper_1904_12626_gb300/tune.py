@@ -50,7 +50,7 @@ CACHE_VERSION = 1
 TOL = {"fp32": 1e-3, "fp64": 1e-9}
 TILE_ROWS = {"fp32": (1024, 2048, 4096, 8192, 16384, 32768), "fp64": (1024, 2048, 4096, 8192)}
 DEFAULT_TILE_ROWS = {"fp32": 16384, "fp64": 4096}   # the library's defaults
-DEFAULT_TILE_ROWS_AB_FP32 = 4096                     # FP32-mixed AB-joins (shorter tiles)
+DEFAULT_TILE_ROWS_AB_FP32 = 2048                     # FP32-mixed AB-joins (shorter tiles)
 ANCHOR_DIVISORS = (2, 4, 8)
 TOP_VARIANTS = 2
 
