@@ -577,76 +577,89 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
     float rlt = 0.0f;                           // lane u: the top's lower bound
     unsigned bandrows = 0u;                     // rows whose top needs exact comparison
 
-    // pass 1: bounds only
+    // pass 1: bounds only.  A row no lane hits (no cell at its row's or its
+    // column's threshold) only advances the recurrence; the window of open
+    // column slots shifts only while some lane holds one.
+    bool open = false;                          // this lane holds an open slot
 #pragma unroll 1
     for (int u = 0; u < D; ++u) {
         const float4 rw = sRow[s + u];
         const long long i = r + s + u;
         float U[D];
-        unsigned long long top = 0ull;
+        bool hit = false;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
             c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
             c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
             U[d] = cell_score<RAW>(c0.v[d], cc.z, rw.z);
-            if (U[d] >= cc.w) {
-                if (U[d] > aU[d]) {
-                    a2[d] = aU[d];
-                    aU[d] = U[d];
-                    aW[d] = RAW ? 2.0f * ebias : 2.0f * ebias * cc.z * rw.z;
-                    au[d] = u;
-                } else if (U[d] > a2[d]) {
-                    a2[d] = U[d];
+            hit |= (U[d] >= cc.w) | (U[d] >= rw.w);
+        }
+        if (__any_sync(0xffffffffu, hit)) {
+            unsigned long long top = 0ull;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
+                if (U[d] >= cc.w) {
+                    open = true;
+                    if (U[d] > aU[d]) {
+                        a2[d] = aU[d];
+                        aU[d] = U[d];
+                        aW[d] = RAW ? 2.0f * ebias : 2.0f * ebias * cc.z * rw.z;
+                        au[d] = u;
+                    } else if (U[d] > a2[d]) {
+                        a2[d] = U[d];
+                    }
+                }
+                if (U[d] >= rw.w) {
+                    const unsigned long long p = TraitsF32::pack(U[d], i + kl + d);
+                    if (p > top) top = p;
                 }
             }
-            if (U[d] >= rw.w) {
-                const unsigned long long p = TraitsF32::pack(U[d], i + kl + d);
-                if (p > top) top = p;
+            // rows hit only through columns skip the row reduction
+            if (__any_sync(0xffffffffu, top != 0ull)) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
+                    if (y > top) top = y;
+                }
+                const long long jt = TraitsF32::pidx(top);     // warp-uniform
+                const float czt = sCol[cpos<D>((int)(jt - r - k0))].z;
+                const float lt = TraitsF32::pval(top) - (RAW ? 2.0f * ebias : 2.0f * ebias * czt * rw.z);
+                bool band = false;
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    band |= (U[d] >= rw.w) && (i + kl + d != jt) && (U[d] >= lt);
+                if (__any_sync(0xffffffffu, band)) bandrows |= 1u << u;
+                if (lane == u) {
+                    rtop = top;
+                    rlt = lt;
+                }
             }
         }
-        // most replayed rows have no cell at the row's threshold: skip the reduction
-        if (!__any_sync(0xffffffffu, top != 0ull)) {
-            top = 0ull;
-        } else {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, top, o);
-                if (y > top) top = y;
+        if (__any_sync(0xffffffffu, open)) {
+            // slot u is closed: list it, shift the window
+            if (au[0] >= 0) {
+                lV[ln] = aU[0];
+                lL[ln] = aU[0] - aW[0];
+                lmeta[ln] = u | (au[0] << 5) | ((a2[0] >= aU[0] - aW[0]) ? 1 << 10 : 0);
+                ++ln;
             }
-        }
-        if (top != 0ull) {                      // warp-uniform
-            const long long jt = TraitsF32::pidx(top);
-            const float czt = sCol[cpos<D>((int)(jt - r - k0))].z;
-            const float lt = TraitsF32::pval(top) - (RAW ? 2.0f * ebias : 2.0f * ebias * czt * rw.z);
-            bool band = false;
 #pragma unroll
-            for (int d = 0; d < D; ++d)
-                band |= (U[d] >= rw.w) && (i + kl + d != jt) && (U[d] >= lt);
-            if (__any_sync(0xffffffffu, band)) bandrows |= 1u << u;
-            if (lane == u) {
-                rtop = top;
-                rlt = lt;
+            for (int d = 0; d + 1 < D; ++d) {
+                aU[d] = aU[d + 1];
+                aW[d] = aW[d + 1];
+                a2[d] = a2[d + 1];
+                au[d] = au[d + 1];
             }
-        }
-        // slot u is closed: list it, shift the window
-        if (au[0] >= 0) {
-            lV[ln] = aU[0];
-            lL[ln] = aU[0] - aW[0];
-            lmeta[ln] = u | (au[0] << 5) | ((a2[0] >= aU[0] - aW[0]) ? 1 << 10 : 0);
-            ++ln;
-        }
+            aU[D - 1] = -INFINITY;
+            a2[D - 1] = -INFINITY;
+            aW[D - 1] = 0.0f;
+            au[D - 1] = -1;
+            open = false;
 #pragma unroll
-        for (int d = 0; d + 1 < D; ++d) {
-            aU[d] = aU[d + 1];
-            aW[d] = aW[d + 1];
-            a2[d] = a2[d + 1];
-            au[d] = au[d + 1];
+            for (int d = 0; d + 1 < D; ++d) open |= au[d] >= 0;
         }
-        aU[D - 1] = -INFINITY;
-        a2[D - 1] = -INFINITY;
-        aW[D - 1] = 0.0f;
-        au[D - 1] = -1;
     }
 #pragma unroll
     for (int d = 0; d + 1 < D; ++d)             // slots D .. 2D-2
