@@ -1098,23 +1098,41 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
                 float hm[2] = {0.f, 0.f};
                 const long long cb = r + k0;
                 const int ncols = nrr + TD;
+                // (loops kept rolled: this code runs once per chunk, and its
+                // instructions are mostly fetched cold)
+#pragma unroll 1
                 for (int t = threadIdx.x; t < nrr; t += NT)
                     if (index_ok(hdr, r + t, lR + kPad)) stage_async(sRow + t, rS + r + t);
+#pragma unroll 1
                 for (int t = threadIdx.x; t < ncols; t += NT)
                     if (index_ok(hdr, cb + t, lC + kPad)) stage_async(sCol + cpos<D>(t), cS + cb + t);
                 stage_wait();
                 if (Tr::kBias) {                       // this thread's own entries
+#pragma unroll 1
                     for (int t = threadIdx.x; t < nrr; t += NT) track_max<RAW>(mx, hm, sRow[t]);
+#pragma unroll 1
                     for (int t = threadIdx.x; t < ncols; t += NT) track_max<RAW>(mx + 4, hm + 1, sCol[cpos<D>(t)]);
                 }
-                if (Tr::kBias) {                       // warp sums, then one add per warp
+                if (Tr::kBias) {
+                    // warp sums of the 8 quantities by a transposing butterfly:
+                    // each exchange halves the values a lane carries, so lane L
+                    // ends with the sum of quantity 4 b4 + 2 b3 + b2 (b = bits of L)
+                    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+                    float w4[4], w2[2];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        float v = mx[k];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0 && v > 0.f) atomicAdd(&s_mx[par + k], v);
+                    for (int j = 0; j < 4; ++j) {
+                        const float keep = h4 ? mx[j + 4] : mx[j], send = h4 ? mx[j] : mx[j + 4];
+                        w4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                     }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float keep = h3 ? w4[j + 2] : w4[j], send = h3 ? w4[j] : w4[j + 2];
+                        w2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+                    float v = (h2 ? w2[1] : w2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? w2[0] : w2[1], 4);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    if ((lane & 3) == 0 && v > 0.f) atomicAdd(&s_mx[par + (lane >> 2)], v);
                     if (RAW) {                         // h >= 0: integer max on the bits
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
@@ -1136,6 +1154,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
             // columns (the fast path's column test)
             {
                 constexpr int NQ = col_quarters<Tr, D>(), RQ = D / NQ;
+#pragma unroll 1
                 for (int q8 = threadIdx.x; q8 * D < nrr + TD; q8 += NT) {
                     T mn[4] = {Tr::inf(), Tr::inf(), Tr::inf(), Tr::inf()};
 #pragma unroll
