@@ -596,7 +596,8 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
             hit |= (U[d] >= cc.w) | (U[d] >= rw.w);
         }
         if (__any_sync(0xffffffffu, hit)) {
-            unsigned long long top = 0ull;
+            float M = -INFINITY;                // the lane's largest cell (lowest column on
+            int dm = 0;                         // ties; NaN never wins)
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
@@ -611,11 +612,12 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
                         a2[d] = U[d];
                     }
                 }
-                if (U[d] >= rw.w) {
-                    const unsigned long long p = TraitsF32::pack(U[d], i + kl + d);
-                    if (p > top) top = p;
+                if (U[d] > M) {
+                    M = U[d];
+                    dm = d;
                 }
             }
+            unsigned long long top = M >= rw.w ? TraitsF32::pack(M, i + kl + dm) : 0ull;
             // rows hit only through columns skip the row reduction
             if (__any_sync(0xffffffffu, top != 0ull)) {
 #pragma unroll
@@ -690,33 +692,39 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
             const long long i = r + s + u;
             const bool rb = (bandrows >> u) & 1u;
             const float ltu = __shfl_sync(0xffffffffu, rlt, u);
-            unsigned long long rbest = 0ull;
+            unsigned ms = 0u, mr = 0u;          // this lane's cells (bit d) needing an exact value
 #pragma unroll
             for (int d = 0; d < D; ++d) {
                 const float4 cc = sCol[cpos<D>(lane_off + s + u + d)];
                 c0.v[d] = fmaf(rw.x, cc.y, c0.v[d]);
                 c0.v[d] = fmaf(cc.x, rw.y, c0.v[d]);
                 const float Uc = cell_score<RAW>(c0.v[d], cc.z, rw.z);
-                const int o = u + d;
-                const bool need_s = Uc >= lo_l[o];
-                const bool need_r = rb && Uc >= ltu;
-                unsigned mask = __ballot_sync(0xffffffffu, need_s || need_r);
-                while (mask) {
-                    const int src = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const long long j = __shfl_sync(0xffffffffu, i + kl + d, src);
-                    const bool ns = __shfl_sync(0xffffffffu, need_s, src);
-                    const bool nr = __shfl_sync(0xffffffffu, need_r, src);
-                    const bool ok = index_ok(hdr, i, P.lR) & index_ok(hdr, j, P.lC);
-                    const float e = ok ? (float)exact_correlation(P, i, j, lane) : 0.0f;
-                    if (ns && lane == src) {
-                        const unsigned long long p = TraitsF32::pack(e, i);
-                        if (p > ex_l[o]) ex_l[o] = p;
-                    }
-                    if (nr) {
-                        const unsigned long long p = TraitsF32::pack(e, j);
-                        if (p > rbest) rbest = p;
-                    }
+                if (Uc >= lo_l[u + d]) ms |= 1u << d;
+                if (rb && Uc >= ltu) mr |= 1u << d;
+            }
+            // the warp's pending cells, one at a time (lowest lane, then lowest d)
+            unsigned long long rbest = 0ull;
+            unsigned pend = ms | mr;
+#pragma unroll 1
+            for (;;) {
+                const unsigned has = __ballot_sync(0xffffffffu, pend != 0u);
+                if (!has) break;
+                const int src = __ffs(has) - 1;
+                const int d = __shfl_sync(0xffffffffu, __ffs(pend) - 1, src);
+                const unsigned bit = 1u << d;
+                const long long j = __shfl_sync(0xffffffffu, kl, src) + i + d;
+                const bool ns = (__shfl_sync(0xffffffffu, ms, src) & bit) != 0u;
+                const bool nr = (__shfl_sync(0xffffffffu, mr, src) & bit) != 0u;
+                if (lane == src) pend &= ~bit;
+                const bool ok = index_ok(hdr, i, P.lR) & index_ok(hdr, j, P.lC);
+                const float e = ok ? (float)exact_correlation(P, i, j, lane) : 0.0f;
+                if (ns && lane == src) {
+                    const unsigned long long p = TraitsF32::pack(e, i);
+                    if (p > ex_l[u + d]) ex_l[u + d] = p;
+                }
+                if (nr) {
+                    const unsigned long long p = TraitsF32::pack(e, j);
+                    if (p > rbest) rbest = p;
                 }
             }
             if (lane == u && rb) rex = rbest;
