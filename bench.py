@@ -297,6 +297,13 @@ def workspace_tiles(ws) -> int:
     return int(ws[24:32].cpu().numpy().view(np.uint64)[0])
 
 
+def workspace_tile_diags(ws) -> int:
+    """Diagonals per band of the tile shape the last join on `ws` ran (the
+    workspace header's bytes 20..23): the library's choice when the variant
+    was left to it."""
+    return int(ws[20:24].cpu().numpy().view(np.int32)[0])
+
+
 def fp64_roofline(cells, kernel_ms, anchor_fma, torch):
     """The all-FP64 tile kernel against the FP64 pipe, whose rate the library's
     probe measures on this GPU (mp_probe_fp64_rate: DFMA from independent
@@ -395,13 +402,18 @@ def run_ours(args, world, rank, local):
     # fragile pass, finalize)
     seed_launches = 3 if args.prec == "fp32" else 1
     launches_per_step = (7 + seed_launches + 10) if anytime else (8 + seed_launches)
-    td, rc = ctypes.c_int32(), ctypes.c_int32()
     prec_id = 1 if args.prec == "fp32" else 0
-    variant = cfg.variant if cfg.variant >= 0 else 0     # the library's choice for a self-join
-    _lib.check(lib.mp_variant_info(prec_id, variant, ctypes.byref(td), ctypes.byref(rc)),
-               "mp_variant_info")
-    kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> variant {variant} "
-                   f"({td.value} diagonals x {rc.value}-row chunks)")
+    td = workspace_tile_diags(ws)                        # the shape the library ran
+    variant = cfg.variant
+    if variant < 0:                                      # the library's choice: the variant
+        for v in range(int(lib.mp_variant_count(prec_id))):   # of that shape
+            tdv, rcv = ctypes.c_int32(), ctypes.c_int32()
+            _lib.check(lib.mp_variant_info(prec_id, v, ctypes.byref(tdv), ctypes.byref(rcv)), "mp_variant_info")
+            if tdv.value == td:
+                variant = v
+    kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> "
+                   f"{'variant ' + str(variant) if cfg.variant >= 0 else 'library choice'} "
+                   f"({td} diagonals per band)")
     step_ms, kern_ms = [], []
     kms = ctypes.c_float()
     barrier(world)
@@ -453,9 +465,8 @@ def run_ours(args, world, rank, local):
         out64 = [t.cpu().numpy() for t in api.selfjoin(x, m, 0.5, "fp64", ws=ws64)]
         torch.cuda.synchronize()
         tiles64 = workspace_tiles(ws64)
-        td64 = ctypes.c_int32()
-        _lib.check(lib.mp_variant_info(0, 0, ctypes.byref(td64), ctypes.byref(rc)), "mp_variant_info")
-        fp64["roofline"] = fp64_roofline(cells, kern64, tiles64 * td64.value * m, torch)
+        td64 = workspace_tile_diags(ws64)
+        fp64["roofline"] = fp64_roofline(cells, kern64, tiles64 * td64 * m, torch)
         del ws64
 
     # end to end through the public API: pinned host input in, MP/PI back to host
@@ -525,8 +536,8 @@ def run_ours(args, world, rank, local):
                      "flop_frac": 6 * cells_per_s_kernel / (sms * 256 * f_max * 1e6),
                      "frac_at_median_clock": (achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
                                               if clocks.get("sm_mhz") else None),
-                     "anchors": {"tiles": tiles32, "ffma": tiles32 * td.value * m,
-                                 "ffma_per_cell": tiles32 * td.value * m / cells,
+                     "anchors": {"tiles": tiles32, "ffma": tiles32 * td * m,
+                                 "ffma_per_cell": tiles32 * td * m / cells,
                                  "note": "dot products at each tile's first row: m FP32 "
                                          "multiply-adds per diagonal on values centred in "
                                          "FP64 (about 1.5 more FP32 instructions per term for "

@@ -86,8 +86,9 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * defaults to 2048 rows, the pan profile to 4096).  variant: compiled tile
  * shape (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the
  * library's choice: variant 7 (four warps per CTA, 5 CTAs per SM) for
- * FP32-mixed AB-joins, variant 1 (four warps per CTA) for FP32-mixed batched
- * and pan joins, variant 0 otherwise.  These
+ * FP32-mixed joins, variant 1 (four warps per CTA, 4 CTAs per SM) for
+ * FP32-mixed pan profiles, variant 0 for the FP64 path and the
+ * non-normalised distance.  These
  * three set the speed: the FP32-mixed path returns the same neighbours under
  * every setting, the FP64 path may break ties closer than its rounding
  * differently.  flags: MP_FLAG_*.
@@ -234,7 +235,7 @@ mp_status mp_fluss(const int64_t *pi, int64_t l, int64_t edge, int32_t num_segme
  * until the process exits; nothing is allocated by any call.
  * Size limit: the series' mp_selfjoin workspace must fit in the 64 MiB, about
  * 97 bytes per sample with the FP32-mixed precision and 81 with FP64 (plus the
- * tile plan): n up to 690,064 (FP32-mixed) or 826,400 (FP64) with the
+ * tile plan): n up to 690,456 (FP32-mixed) or 826,400 (FP64) with the
  * default tile shapes; mp_selfjoin_noalloc_max_n(cfg) returns the exact
  * largest n for a configuration (0 for an invalid one).  A larger n returns MP_ENOMEM before
  * any work is enqueued.

@@ -12,6 +12,7 @@ using namespace mpgb;
 namespace {
 
 constexpr int kMaxDevices = 64;
+constexpr int kMaxVariants = 16;          // compiled tile shapes per precision, at most
 constexpr int kDefaultTileRowsF32 = 16384;
 constexpr int kDefaultTileRowsF64 = 4096;
 // FP32-mixed AB-joins: shorter row tiles by default.  Both series' keys improve
@@ -21,14 +22,15 @@ constexpr int kDefaultTileRowsF64 = 4096;
 // 2048 / 4096 / 8192 rows: variant 0 358 / 347 / 355 / 476, variant 7 333 / 323
 // / 331 / 445).
 constexpr int kDefaultTileRowsAbF32 = 2048;
-// The tile shape MP_VARIANT_AUTO stands for in FP32-mixed AB-joins: four warps
-// per CTA at 5 CTAs per SM (variant 7, figures above).
-constexpr int kAutoVariantAb = 7;
-// The tile shape MP_VARIANT_AUTO stands for in the batched and pan joins: four
-// warps per CTA (1024 diagonals per band; on 4096 ragged walks 1941 ms against
-// 2024 ms with the two-warp default, on 64 window sizes of a 2^16 walk 111
-// against 117 ms at 4096-row tiles).  The self-, left/right and AB-joins keep 0.
-constexpr int kAutoVariantFamilies = 1;
+
+// The tile shape MP_VARIANT_AUTO stands for in FP32-mixed joins: four warps per
+// CTA at 5 CTAs per SM (variant 7; 1024 diagonals per band).  Tile kernel ms,
+// variant 0 / 7 at the default heights: self-join 2^20 (m = 256) 106.6 / 102.9,
+// AB 2^21 x 2^19 (m = 512) 295 / 264, 4096 ragged walks 1335 / 1300, gradient
+// input 2^16 (m = 128) 1.40 / 1.36.  Pan profiles take variant 1 (four warps, 4
+// CTAs per SM): 68.9 ms against 69.6 (variant 7) and 73.9 (variant 0).
+constexpr int kAutoVariantF32 = 7;
+constexpr int kAutoVariantPan = 1;
 // FP32-mixed pan profiles: 4096-row tiles by default, for the AB-join's reason
 // (variant 1: 111 ms against 114 ms at 16384 rows)
 constexpr int kDefaultTileRowsPanF32 = 4096;
@@ -40,8 +42,8 @@ struct DeviceInfo {
     bool ev_used = false;
     bool ok = false;
     int sms = 0;
-    int f32_bps[8] = {0};
-    int f64_bps[8] = {0};
+    int f32_bps[kMaxVariants] = {0};
+    int f64_bps[kMaxVariants] = {0};
     int f32_raw_bps = 0, f64_raw_bps = 0;       // MP_FLAG_RAW kernels (variant 0 shape)
 };
 DeviceInfo g_dev[kMaxDevices];
@@ -63,8 +65,8 @@ mp_status device_info(int dev, const DeviceInfo **out)
             int cur = -1;
             cudaGetDevice(&cur);
             if (cur != dev) cudaSetDevice(dev);
-            for (int v = 0; v < f32_variant_count() && v < 8; ++v) d.f32_bps[v] = f32_blocks_per_sm(v);
-            for (int v = 0; v < f64_variant_count() && v < 8; ++v) d.f64_bps[v] = f64_blocks_per_sm(v);
+            for (int v = 0; v < f32_variant_count() && v < kMaxVariants; ++v) d.f32_bps[v] = f32_blocks_per_sm(v);
+            for (int v = 0; v < f64_variant_count() && v < kMaxVariants; ++v) d.f64_bps[v] = f64_blocks_per_sm(v);
             d.f32_raw_bps = f32_raw_blocks_per_sm();
             d.f64_raw_bps = f64_raw_blocks_per_sm();
             if (cur != dev && cur >= 0) cudaSetDevice(cur);
@@ -98,7 +100,7 @@ struct TileCfg {
 
 // auto_variant: the tile shape MP_VARIANT_AUTO stands for in this family
 // (FP32-mixed only; the FP64 path and the non-normalised distance take 0)
-mp_status resolve(const mp_config *cfg, TileCfg *t, int auto_variant = 0)
+mp_status resolve(const mp_config *cfg, TileCfg *t, int auto_variant = kAutoVariantF32)
 {
     if (!cfg) return MP_EINVAL;
     if (cfg->prec != MP_PREC_FP64 && cfg->prec != MP_PREC_FP32_MIXED) return MP_EINVAL;
@@ -108,6 +110,7 @@ mp_status resolve(const mp_config *cfg, TileCfg *t, int auto_variant = 0)
     const bool raw_flag = (cfg->flags & MP_FLAG_RAW) != 0;
     t->variant = cfg->variant >= 0 ? cfg->variant
                                    : ((t->fp64 || raw_flag) ? 0 : auto_variant);
+    if (t->variant >= kMaxVariants) return MP_EUNSUPPORTED;
     int threads = 0, smem = 0;
     const bool ok = t->fp64 ? f64_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem)
                             : f32_variant_info(t->variant, &t->tile_diags, &t->chunk_rows, &threads, &smem);
@@ -577,7 +580,7 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
 size_t mp_abjoin_workspace_bytes(int64_t na, int64_t nb, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t, kAutoVariantAb) != MP_OK || na < 1 || nb < 1) return 0;
+    if (resolve(cfg, &t) != MP_OK || na < 1 || nb < 1) return 0;
     return carve(nullptr, ab_req(na, nb, cfg->m, t)).bytes;
 }
 
@@ -588,7 +591,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
     TileCfg t;
     if (!a || !b || !mp_a || !pi_a || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
     if ((mp_b == nullptr) != (pi_b == nullptr)) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t, kAutoVariantAb);
+    mp_status s = resolve(cfg, &t);
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > na || (int64_t)m > nb || na > kMaxN || nb > kMaxN) return MP_EINVAL;
@@ -621,7 +624,7 @@ mp_status mp_abjoin(const void *a, int64_t na, const void *b, int64_t nb, int32_
 size_t mp_pan_workspace_bytes(int64_t n, const int32_t *ms, int32_t nm, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t, kAutoVariantFamilies) != MP_OK || !ms || nm < 1 || nm > kMaxPan || n < 1) return 0;
+    if (resolve(cfg, &t, kAutoVariantPan) != MP_OK || !ms || nm < 1 || nm > kMaxPan || n < 1) return 0;
     for (int k = 0; k < nm; ++k)
         if (ms[k] < 4 || ms[k] > n) return 0;
     return carve(nullptr, pan_req(n, ms, nm, t)).bytes;
@@ -639,7 +642,7 @@ mp_status mp_pan(const void *x, int32_t dtype, int64_t n, const int32_t *ms, int
         if (ms[k] < 4 || (int64_t)ms[k] > n) return MP_EINVAL;
         if (ms[k] < mmin) mmin = ms[k];
     }
-    mp_status s = resolve(cfg, &t, kAutoVariantFamilies);
+    mp_status s = resolve(cfg, &t, kAutoVariantPan);
     if (s != MP_OK) return s;
     const LayoutReq r = pan_req(n, ms, nm, t);
     const Layout L = carve(ws, r);
@@ -673,7 +676,7 @@ size_t mp_batched_workspace_bytes(int64_t total_values, int32_t B, int32_t max_m
 {
     TileCfg t;
     (void)max_m;
-    if (resolve(cfg, &t, kAutoVariantFamilies) != MP_OK || B < 1 || total_values < 0) return 0;
+    if (resolve(cfg, &t) != MP_OK || B < 1 || total_values < 0) return 0;
     return carve(nullptr, batched_req(total_values, B, t)).bytes;
 }
 
@@ -687,7 +690,7 @@ mp_status mp_batched(const void *values, int32_t dtype, int64_t total_values,
         !aligned256(ws))
         return MP_EINVAL;
     if (B < 1 || B > 65535 || total_values < 1 || total_values > kMaxN || max_m < 4) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t, kAutoVariantFamilies);
+    mp_status s = resolve(cfg, &t);
     if (s != MP_OK) return s;
     const LayoutReq r = batched_req(total_values, B, t);
     const Layout L = carve(ws, r);

@@ -67,7 +67,7 @@ struct Hdr {
     unsigned long long ticket;            // tile ticket counter of the persistent kernel
     int nbands;                           // bands the tile kernel may take (a prefix of the
                                           // band order; all of them unless anytime)
-    int pad1;
+    int tile_diags;                       // diagonals per band of the planned tile shape
     unsigned long long ntiles;            // number of tiles (same as tile_prefix[nbands])
     unsigned long long frag_count;        // fragile windows found (FP32-mixed path)
     long long band_total;                 // anytime: bands planned

@@ -127,6 +127,7 @@ __global__ void plan_kernel(const Prob *__restrict__ probs, int nprob, int TD, i
     block_exclusive_scan<unsigned long long>(tile_prefix, total);
     if (threadIdx.x == 0) {
         hdr->nbands = (int)total;
+        hdr->tile_diags = TD;
         hdr->ntiles = tile_prefix[total];
         hdr->ticket = 0ull;
     }

@@ -117,10 +117,13 @@ def test_anytime_full_size_five_percent(mp):
     x, info = synth.planted_walk(n, m, seed=2024)
     l = n - m + 1
     E = oracle.exclusion_zone(m)
-    td = _tile_diags("fp32", 0)
+    run = mp.Anytime(torch.from_numpy(x).cuda(), m, seed=seed)
+    # the tile shape the library chose: the workspace header records its
+    # diagonals per band (bytes 20..23)
+    td = int(run.ws[20:24].cpu().numpy().view(np.int32)[0])
+    assert td == _tile_diags("fp32", 7)
     nb = (l - 1 - E) // td + 1
     perm = band_order(nb, seed)
-    run = mp.Anytime(torch.from_numpy(x).cuda(), m, seed=seed)
     g_mp, g_pi = (t.cpu().numpy() for t in run.run(0.05, check_status=True))
     ok = diag_mask(l, E, td, perm, math.ceil(0.05 * nb))
     rows = synth.sample_rows(l, 48, seed=43)

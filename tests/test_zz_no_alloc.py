@@ -80,7 +80,7 @@ def test_size_limit(lib):
     l = lib.load()
     cfg = lib.make_config(64, 0.5, "fp32")
     n_max = l.mp_selfjoin_noalloc_max_n(ctypes.byref(cfg))
-    assert n_max == 690_064                # the figure the header states
+    assert n_max == 690_456                # the figure the header states
     assert l.mp_selfjoin_noalloc_max_n(ctypes.byref(lib.make_config(64, 0.5, "fp64"))) == 826_400
     x = torch.from_numpy(synth.random_walk(n_max, seed=33, dtype=np.float32)).cuda()
     mp_a, pi_a = _noalloc(lib, x, cfg)
