@@ -402,17 +402,9 @@ def run_ours(args, world, rank, local):
     # fragile pass, finalize)
     seed_launches = 3 if args.prec == "fp32" else 1
     launches_per_step = (7 + seed_launches + 10) if anytime else (8 + seed_launches)
-    prec_id = 1 if args.prec == "fp32" else 0
     td = workspace_tile_diags(ws)                        # the shape the library ran
-    variant = cfg.variant
-    if variant < 0:                                      # the library's choice: the variant
-        for v in range(int(lib.mp_variant_count(prec_id))):   # of that shape
-            tdv, rcv = ctypes.c_int32(), ctypes.c_int32()
-            _lib.check(lib.mp_variant_info(prec_id, v, ctypes.byref(tdv), ctypes.byref(rcv)), "mp_variant_info")
-            if tdv.value == td:
-                variant = v
     kernel_name = (f"join_tile_kernel<Traits{args.prec.upper()}> "
-                   f"{'variant ' + str(variant) if cfg.variant >= 0 else 'library choice'} "
+                   f"{'variant ' + str(cfg.variant) if cfg.variant >= 0 else 'library choice'} "
                    f"({td} diagonals per band)")
     step_ms, kern_ms = [], []
     kms = ctypes.c_float()
@@ -816,7 +808,7 @@ def run_grad(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": issue_peak,
                      "unit": "T FP32 lane-instructions/s (6 per cell: 2 FFMA, 2 FMUL, 2 FSETP)",
                      "frac": achieved / issue_peak, "traffic": None,
-                     "kernel": "join_tile_kernel<TraitsFP32> variant 0 (forward)",
+                     "kernel": "join_tile_kernel<TraitsFP32>, the library's tile shape (forward)",
                      "kernel_ms": kernel_ms},
         "backward": {"ms": bwd_ms, "rows": l, "fp64_atomic_adds": 2 * m * l,
                      "atomic_adds_per_s": 2 * m * l / (bwd_ms / 1e3)},

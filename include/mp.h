@@ -86,7 +86,9 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * defaults to 2048 rows, the pan profile to 4096).  variant: compiled tile
  * shape (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the
  * library's choice: variant 7 (four warps per CTA, 5 CTAs per SM) for
- * FP32-mixed joins, variant 1 (four warps per CTA, 4 CTAs per SM) for
+ * FP32-mixed joins, variant 3 (four warps, 256-row chunks) for FP32-mixed
+ * self-joins, left/right and anytime runs of fewer than about 4e9 cells
+ * ((n - m + 1)^2 / 2), variant 1 (four warps per CTA, 4 CTAs per SM) for
  * FP32-mixed pan profiles, variant 0 for the FP64 path and the
  * non-normalised distance.  These
  * three set the speed: the FP32-mixed path returns the same neighbours under

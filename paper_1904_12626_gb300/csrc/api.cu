@@ -31,6 +31,15 @@ constexpr int kDefaultTileRowsAbF32 = 2048;
 // CTAs per SM): 68.9 ms against 69.6 (variant 7) and 73.9 (variant 0).
 constexpr int kAutoVariantF32 = 7;
 constexpr int kAutoVariantPan = 1;
+// Small self-joins (and left/right and anytime runs) take variant 3 (four
+// warps, 256-row chunks, 4 CTAs per SM): a persistent grid of 760 CTAs has few
+// tiles to share there.  Tile kernel ms, variant 3 / 7, random walks, m = 64,
+// 128, 256: 2^14 windows 0.80 / 0.99, 0.73 / 0.84, 0.99 / 1.07; 2^15 0.71 /
+// 0.96, 0.74 / 0.94, 1.07 / 1.20; 2^16 1.20 / 1.37, 1.22 / 1.36, 1.48 / 1.71;
+// 2^17 3.03 / 2.98, 2.99 / 2.95, 3.27 / 3.31; 2^18 9.50 / 8.75, 9.22 / 8.44,
+// 9.77 / 9.08.  The two cross near 2^17 windows, about 8e9 cells.
+constexpr int kAutoVariantSmall = 3;
+constexpr double kSmallJoinCells = 4.0e9;
 // FP32-mixed pan profiles: 4096-row tiles by default, for the AB-join's reason
 // (variant 1: 111 ms against 114 ms at 16384 rows)
 constexpr int kDefaultTileRowsPanF32 = 4096;
@@ -125,6 +134,14 @@ mp_status resolve(const mp_config *cfg, TileCfg *t, int auto_variant = kAutoVari
     t->raw = (cfg->flags & MP_FLAG_RAW) != 0;
     if (t->raw && t->variant != 0) return MP_EUNSUPPORTED;
     return MP_OK;
+}
+
+// The tile shape MP_VARIANT_AUTO stands for in a self-join of n samples.
+int self_auto_variant(int64_t n, const mp_config *cfg)
+{
+    if (!cfg) return kAutoVariantF32;
+    const double l = (double)(n - cfg->m + 1);
+    return (l > 0.0 && 0.5 * l * l < kSmallJoinCells) ? kAutoVariantSmall : kAutoVariantF32;
 }
 
 // Row-tile height of a join whose caller left it to the library.  The tile
@@ -427,7 +444,7 @@ mp_status mp_stats(const void *x, int32_t dtype, int64_t n, int32_t m, double *m
 size_t mp_selfjoin_workspace_bytes(int64_t n, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t) != MP_OK || n < 1) return 0;
+    if (resolve(cfg, &t, self_auto_variant(n, cfg)) != MP_OK || n < 1) return 0;
     return carve(nullptr, self_req(n, cfg->m, t)).bytes;
 }
 
@@ -436,7 +453,7 @@ mp_status mp_selfjoin(const void *x, int32_t dtype, int64_t n, const mp_config *
 {
     TileCfg t;
     if (!x || !mp || !pi || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, self_auto_variant(n, cfg));
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
@@ -469,7 +486,7 @@ mp_status mp_anytime_begin(const void *x, int32_t dtype, int64_t n, const mp_con
 {
     TileCfg t;
     if (!x || !ws || !valid_dtype(dtype) || !aligned256(ws)) return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, self_auto_variant(n, cfg));
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
@@ -500,7 +517,7 @@ mp_status mp_anytime_run(int64_t n, const mp_config *cfg, double fraction, doubl
     TileCfg t;
     if (!mp || !pi || !ws || !aligned256(ws) || !(fraction >= 0.0 && fraction <= 1.0))
         return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, self_auto_variant(n, cfg));
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
@@ -541,7 +558,7 @@ mp_status mp_fluss(const int64_t *pi, int64_t l, int64_t edge, int32_t num_segme
 size_t mp_selfjoin_lr_workspace_bytes(int64_t n, const mp_config *cfg)
 {
     TileCfg t;
-    if (resolve(cfg, &t) != MP_OK || n < 1) return 0;
+    if (resolve(cfg, &t, self_auto_variant(n, cfg)) != MP_OK || n < 1) return 0;
     return carve(nullptr, lr_req(n, cfg->m, t)).bytes;
 }
 
@@ -553,7 +570,7 @@ mp_status mp_selfjoin_lr(const void *x, int32_t dtype, int64_t n, const mp_confi
     if (!x || !mp_left || !pi_left || !mp_right || !pi_right || !ws || !valid_dtype(dtype) ||
         !aligned256(ws))
         return MP_EINVAL;
-    mp_status s = resolve(cfg, &t);
+    mp_status s = resolve(cfg, &t, self_auto_variant(n, cfg));
     if (s != MP_OK) return s;
     const int32_t m = cfg->m;
     if (m < 4 || (int64_t)m > n || n > kMaxN) return MP_EINVAL;
