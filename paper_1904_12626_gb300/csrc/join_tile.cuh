@@ -803,8 +803,15 @@ __device__ __forceinline__ void replay_group_f32(const Prob &P, float4 *sRow, fl
     __syncwarp();
 }
 
-// groups the fast path records before their replays run
-constexpr int kQueue = 16;
+// groups the fast path records before their replays run: a whole 512-row
+// chunk, so a chunk is one pass of the fast path and then its replays in one
+// burst (the replay code runs warm, and the fast path is called once per chunk;
+// tile kernel ms at 16 / 32 / 64 groups, variant 7: self-join 2^20 102.7 /
+// 101.9 / 100.7, AB 263 / 260 / 258, 4096 ragged walks 1297 / 1287 / 1274, pan
+// 68.9 / 67.9 / 66.6).  The FP64 path keeps 16 (its covariances are twice the
+// size, and the recorded groups live in local memory).
+template <class Tr>
+__host__ __device__ constexpr int queue_len() { return Tr::kBias ? 64 : 16; }
 
 // The two halves of a cell's score: the part that depends on the column,
 // t = c invn_j (RAW: c - h_j), and the row's factor applied to it,
@@ -1030,6 +1037,7 @@ join_tile_kernel(const Prob *__restrict__ probs, const Band *__restrict__ bands,
     const int nb = hdr->nbands;
     const unsigned long long ntiles = tile_prefix[nb];
     const T INF = Tr::inf();
+    constexpr int kQueue = queue_len<Tr>();
     CovArr<T, D> q_c0[kQueue];                 // recorded groups of the current sub-chunk
     int q_s[kQueue];
 
