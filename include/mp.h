@@ -83,13 +83,12 @@ typedef enum { MP_PREC_FP64 = 0, MP_PREC_FP32_MIXED = 1 } mp_precision;
  * FP64, halved down to 1024 for joins too small to keep every CTA of the
  * persistent grid busy with that many; mp_batched keeps the default).
  * Both are rounded up to whole chunks of the variant (the FP32-mixed AB-join
- * defaults to 2048 rows, the pan profile to 4096).  variant: compiled tile
+ * and the pan profile default to 2048 rows).  variant: compiled tile
  * shape (mp_variant_count/mp_variant_info), or MP_VARIANT_AUTO for the
  * library's choice: variant 7 (four warps per CTA, 5 CTAs per SM) for
  * FP32-mixed joins, variant 3 (four warps, 256-row chunks) for FP32-mixed
  * self-joins, left/right and anytime runs of fewer than about 4e9 cells
- * ((n - m + 1)^2 / 2), variant 1 (four warps per CTA, 4 CTAs per SM) for
- * FP32-mixed pan profiles, variant 0 for the FP64 path and the
+ * ((n - m + 1)^2 / 2), variant 0 for the FP64 path and the
  * non-normalised distance.  These
  * three set the speed: the FP32-mixed path returns the same neighbours under
  * every setting, the FP64 path may break ties closer than its rounding

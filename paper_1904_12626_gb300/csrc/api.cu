@@ -27,10 +27,10 @@ constexpr int kDefaultTileRowsAbF32 = 2048;
 // CTA at 5 CTAs per SM (variant 7; 1024 diagonals per band).  Tile kernel ms,
 // variant 0 / 7 at the default heights: self-join 2^20 (m = 256) 106.6 / 102.9,
 // AB 2^21 x 2^19 (m = 512) 295 / 264, 4096 ragged walks 1335 / 1300, gradient
-// input 2^16 (m = 128) 1.40 / 1.36.  Pan profiles take variant 1 (four warps, 4
-// CTAs per SM): 68.9 ms against 69.6 (variant 7) and 73.9 (variant 0).
+// input 2^16 (m = 128) 1.40 / 1.36; pan profiles (64 window sizes of a 2^16
+// walk) at 2048-row tiles 64.1 ms.
 constexpr int kAutoVariantF32 = 7;
-constexpr int kAutoVariantPan = 1;
+constexpr int kAutoVariantPan = 7;
 // Small self-joins (and left/right and anytime runs) take variant 3 (four
 // warps, 256-row chunks, 4 CTAs per SM): a persistent grid of 760 CTAs has few
 // tiles to share there.  Tile kernel ms, variant 3 / 7, random walks, m = 64,
@@ -40,9 +40,10 @@ constexpr int kAutoVariantPan = 1;
 // 9.77 / 9.08.  The two cross near 2^17 windows, about 8e9 cells.
 constexpr int kAutoVariantSmall = 3;
 constexpr double kSmallJoinCells = 4.0e9;
-// FP32-mixed pan profiles: 4096-row tiles by default, for the AB-join's reason
-// (variant 1: 111 ms against 114 ms at 16384 rows)
-constexpr int kDefaultTileRowsPanF32 = 4096;
+// FP32-mixed pan profiles: 2048-row tiles by default, for the AB-join's reason
+// (64 window sizes of a 2^16 walk, tile kernel: variant 7 at 2048 rows 64.1 ms,
+// the autotuner's choice, against 66.8 ms for variant 1 at 4096 rows)
+constexpr int kDefaultTileRowsPanF32 = 2048;
 constexpr long long kMaxN = 2147483647ll;
 
 struct DeviceInfo {
