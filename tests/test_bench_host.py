@@ -25,3 +25,16 @@ def test_cpu_oracle_sample_and_accuracy():
     pi2[r[sep[0]]] = (pi2[r[sep[0]]] + 1000) % len(pi2)
     acc = bench.accuracy(res, mp2, pi2)
     assert abs(acc["max_abs_dmp"] - 2e-4) < 1e-12 and not acc["pi_equal_on_separated"]
+
+
+def test_workspace_header_fields():
+    """The bench reads the plan's tile count (bytes 24..31) and band width
+    (bytes 20..23) from the workspace header; the offsets follow the header's
+    layout: status, pad, ticket (8 bytes), bands (4), band width (4), tiles (8)."""
+    import torch
+    ws = torch.zeros(256, dtype=torch.uint8)
+    ws[20:24] = torch.from_numpy(np.array([1024], dtype=np.int32).view(np.uint8))
+    ws[24:32] = torch.from_numpy(np.array([48520], dtype=np.uint64).view(np.uint8))
+    ws[16:20] = torch.from_numpy(np.array([777], dtype=np.int32).view(np.uint8))
+    assert bench.workspace_tile_diags(ws) == 1024
+    assert bench.workspace_tiles(ws) == 48520
