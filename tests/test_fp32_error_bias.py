@@ -25,7 +25,15 @@ to FP32 is the fused multiply-add) against an FP64 recurrence, and check
 * that an anchor at the drop resets the error, so the bias there could be
   several times narrower;
 * the same bound, plus its worst-case term for the rounding of h and of the
-  score's two subtractions, on the non-normalised path.
+  score's two subtractions, on the non-normalised path;
+* the FP32 anchors: the kernel starts each tile from an FP32 dot product of
+  values centred in FP64 (the row window minus its mean; the column values
+  minus one reference per block of diagonals, staged as FP32 hi + lo pairs
+  and shifted in FP32 to a reference per 8 diagonals) and widens the bias to
+  2 eps hypot(C sqrt(N + 16), B sqrt(m + 4)), B = ||a|| ||b|| the bound on
+  the dot product's partial sums; emulated here step by step, from the FP32
+  anchor against the exact FP64 walk, on random walks and on the same walks
+  shifted by a large offset.
 """
 import math
 
@@ -51,7 +59,44 @@ def _stats(x, m):
     return win, mu, s, df, dg
 
 
-def _walk(a, b, m, k0, width, rows, bias="running", anchor_rows=()):
+def _fma32(acc, x, y):
+    """FP32 fused multiply-add, emulated: the product of two FP32 values is exact
+    in FP64, and the sum is rounded once to FP32."""
+    return np.float32(np.float64(acc) + np.float64(x) * np.float64(y))
+
+
+def _anchor_f32(a, b, m, k0, width, d=8):
+    """The kernel's FP32-mixed anchor at row 0 for diagonals k0..k0+width-1 of
+    row series a against column series b: returns the FP32 covariances and B,
+    the largest over the threads (d diagonals each) of ||a|| ||b_thread||."""
+    f32 = np.float32
+    mu_a = float(np.mean(a[:m]))
+    mu_b = np.lib.stride_tricks.sliding_window_view(b, m).mean(axis=1)
+    at = np.array([f32(v) for v in (a[:m] - mu_a)], dtype=np.float32)
+    g0 = float(mu_b[k0 + width // 2])                   # the block's reference
+    span = b[k0:k0 + width + m - 1].astype(np.float64) - g0
+    hi = span.astype(np.float32)
+    lo = (span - hi.astype(np.float64)).astype(np.float32)
+    c = np.zeros(width, dtype=np.float32)
+    bnd = 0.0
+    for t0 in range(0, width, d):                       # one thread: d diagonals
+        g = float(mu_b[k0 + t0 + d // 2]) - g0
+        g_hi = f32(g)
+        g_lo = f32(g - np.float64(g_hi))
+        bv = ((hi[t0:t0 + m + d - 1] - g_hi).astype(np.float32)
+              + (lo[t0:t0 + m + d - 1] - g_lo).astype(np.float32)).astype(np.float32)
+        for dd in range(d):
+            acc = f32(0.0)
+            for t in range(m):
+                acc = _fma32(acc, at[t], bv[dd + t])
+            c[t0 + dd] = acc
+        sa = float(np.sum(at.astype(np.float64) ** 2))
+        sb = float(np.sum(bv.astype(np.float64) ** 2))
+        bnd = max(bnd, math.sqrt(sa) * math.sqrt(sb))
+    return c, bnd
+
+
+def _walk(a, b, m, k0, width, rows, bias="running", anchor_rows=(), f32_anchor=False):
     """Walk diagonals k0..k0+width-1 (row i of a against column i+k of b) for
     `rows` rows from an anchor at row 0; returns the largest error / bias
     ratio per chunk, and the bias per chunk (correlation units of the
@@ -66,6 +111,10 @@ def _walk(a, b, m, k0, width, rows, bias="running", anchor_rows=()):
     f32 = lambda v: np.asarray(v, np.float32).astype(np.float64)
     c64 = exact(0)
     c32 = c64.astype(np.float32)
+    e_anchor = 0.0
+    if f32_anchor:                                 # the kernel's FP32 anchor
+        c32, bnd = _anchor_f32(a, b, m, k0, width)
+        e_anchor = bnd * math.sqrt(m + 4)
     e_c, steps = 0.0, 0
     ratios, biases = [], []
     for r in range(0, rows, CHUNK):
@@ -79,8 +128,10 @@ def _walk(a, b, m, k0, width, rows, bias="running", anchor_rows=()):
         cur = rms(sA[R]) * rms(sB[C]) + 2 * (rms(dfA[R]) * rms(dgB[C]) + rms(dfB[C]) * rms(dgA[R]))
         e_c = cur if bias == "current" else max(e_c, cur)
         steps += CHUNK
-        E = 2.0 * EPS32 * e_c * math.sqrt(steps + 16)
+        E = 2.0 * EPS32 * math.hypot(e_c * math.sqrt(steps + 16), e_anchor)
         worst = 0.0
+        if r == 0:                                 # the anchor itself
+            worst = float(np.abs(c32.astype(np.float64) - c64).max()) / E
         for i in range(max(r, 1), r + CHUNK):
             j = i + ks
             c64 = c64 + dfA[i] * dgB[j] + dfB[j] * dgA[i]
@@ -181,3 +232,34 @@ def test_raw_bias_covers_fp32_rounding(seed):
     ratios = _walk_raw(x, 256, k0=128, width=64, rows=8192)
     assert ratios.max() < 1.0
     assert ratios.max() > 0.01
+
+
+@pytest.mark.parametrize("seed,offset", [(0, 0.0), (1, 0.0), (2, 1.0e4)])
+def test_bias_covers_fp32_anchor_and_recurrence(seed, offset):
+    """From the FP32 anchor: the anchor's own error and the error after every
+    chunk stay inside the widened bias, also when the series sit on a large
+    offset (the centring is done in FP64, so the offset does not reach the
+    FP32 sums)."""
+    m = 256
+    a = synth.random_walk(6000, seed=seed) + offset
+    b = synth.random_walk(6000, seed=seed + 100) + offset
+    ratios, _ = _walk(a, b, m, k0=128, width=32, rows=2048, f32_anchor=True)
+    assert ratios.max() < 1.0
+    assert ratios.max() > 0.02
+
+
+def test_fp32_anchor_error_is_the_size_the_bias_allows():
+    """The anchor's rounding is of the order of m recurrence steps: the FP32
+    anchor's error alone is a visible fraction of the anchor term of the bias,
+    2 eps B sqrt(m + 4), and well below it."""
+    m = 512
+    a = synth.random_walk(3000, seed=11)
+    b = synth.random_walk(3000, seed=12)
+    c32, bnd = _anchor_f32(a, b, m, k0=64, width=16)
+    win_b = np.lib.stride_tricks.sliding_window_view(b, m)
+    exact = np.array([np.dot(a[:m] - a[:m].mean(), win_b[64 + k] - win_b[64 + k].mean())
+                      for k in range(16)])
+    err = float(np.abs(c32.astype(np.float64) - exact).max())
+    allowance = 2.0 * EPS32 * bnd * math.sqrt(m + 4)
+    assert err < allowance
+    assert err > 1e-3 * allowance
